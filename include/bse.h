@@ -1,0 +1,146 @@
+/*
+ * bse.h -- C ABI of the GB300 (sm_103a) DMPT/TDA Bethe-Salpeter hot path.
+ *
+ * The library applies the Tamm-Dancoff Liouville operator (D + K1e - K1d) of
+ * Eq. (evp) (Yu, Jin, Galli, Govoni, "GPU-Accelerated Solution of the
+ * Bethe-Salpeter Equation for Large and Heterogeneous Systems", Section 2) to
+ * blocks of trial vectors, builds the screened integrals tau_vw of Eqs. (tau),
+ * (tau_from_tau_u) with the low-rank chi_bar of Eq. (pdep), and finds the lowest
+ * vertical excitation energies with a block Davidson solver (Section 3).
+ *
+ * Conventions used by every call
+ * ------------------------------
+ *  - Gamma point, cubic cell of edge L (bohr), FFT grid N^3, real-space index
+ *    r = x + N*(y + N*z) (x fastest). Hartree atomic units.
+ *  - Plane-wave sphere S given by Miller indices miller[n_half][3]: row 0 is
+ *    (0,0,0), rows k >= 1 hold one representative of each {+G_k, -G_k}. Every
+ *    |component| must be <= (N-1)/4 so that all products are alias-free.
+ *  - Gamma-packed real vectors of length n_pw = 2*n_half:
+ *      p[0] = c(0), p[1] = 0 (pad; inputs must hold 0, outputs always hold 0),
+ *      p[2k] = sqrt(2) Re c(G_k), p[2k+1] = sqrt(2) Im c(G_k),
+ *    where f(r) = Omega^{-1/2} sum_{G in S} c(G) e^{iG.r}. Dot products of packed
+ *    vectors equal L2 inner products of the functions.
+ *  - A block of trial vectors is [n_vec][n_occ][n_pw] row-major: the N_occ
+ *    auxiliary orbitals a_{s,v} of each A_s (Eq. evp, Delta rho_s = sum_v |a_sv><psi_v|).
+ *  - v(G) = 4 pi/|G|^2 for G != 0, v(0) = 0, and the head term Xi of Eq. (pdep) is 0.
+ *
+ * Ownership: the caller owns every pointer it passes; input arrays are read during
+ * the call only. The context owns its device buffers (tau, plans, workspaces),
+ * obtained with cudaMalloc, released by bse_destroy. All device work is ordered on
+ * the stream given to bse_create; calls return after that work has completed.
+ *
+ * Errors: every call returns a bse_status. On error no output is valid (except
+ * BSE_ERR_NOT_CONVERGED, see bse_davidson) and bse_last_error() describes it. The
+ * library never traps or aborts; device waits are bounded.
+ */
+#ifndef BSE_H_
+#define BSE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BSE_OK = 0,
+  BSE_ERR_INVALID_ARG = -1,   /* bad size, pointer, or layout */
+  BSE_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+  BSE_ERR_OOM = -3,           /* device allocation failed */
+  BSE_ERR_NUMERIC = -4,       /* non-finite input or breakdown (e.g. Cholesky) */
+  BSE_ERR_NOT_CONVERGED = -5, /* Davidson hit max_it; outputs hold the last Ritz values */
+  BSE_ERR_TIMEOUT = -6,       /* a bounded device wait gave up */
+  BSE_ERR_STATE = -7          /* call order violated (e.g. apply before build_tau) */
+} bse_status;
+
+typedef enum {
+  BSE_PREC_FP64 = 0,   /* plain method: every step in FP64 */
+  BSE_PREC_MIXED = 1   /* FP32 FFTs / pair products / tau streaming, BF16x3 tensor-core
+                          projections with FP32 accumulation, FP64 Davidson algebra */
+} bse_precision;
+
+typedef struct bse_ctx bse_ctx;   /* opaque, library-owned */
+
+/* One Gamma-point system (all host pointers, FP64 unless noted). */
+typedef struct {
+  int n_grid;              /* N: FFT grid N^3; N in {16, 32, 48, 64, 72, 96} */
+  double L;                /* cubic cell edge (bohr) */
+  int n_half;              /* rows of miller */
+  const int32_t* miller;   /* [n_half][3] (x, y, z) integer components of G_k */
+  int n_occ;               /* N_occ occupied orbitals */
+  const double* psi;       /* [n_occ][2*n_half] packed, orthonormal (Section 2, Eq. wannier) */
+  const double* eps;       /* [n_occ] occupied energies eps_v (Ha), Eq. (d) */
+  const double* v_loc;     /* [N^3] local potential samples (Ha), H_KS of Eq. (ham) */
+  double scissor;          /* Delta (Ha): H_QP = H_KS + Delta on the conduction space, Eq. (ham) */
+  int n_pdep;              /* N_PDEP (may be 0: unscreened) */
+  const double* pdep;      /* [n_pdep][2*n_half] packed, orthonormal, entries 0,1 zero (Eq. pdep) */
+  const double* lambda;    /* [n_pdep] PDEP eigenvalues, each in (-1, 0) (Eq. pdep) */
+  double overlap_thr;      /* > 0: keep tau_vw iff O_vw >= overlap_thr (Eq. overlap) */
+  int64_t keep_pairs;      /* used when overlap_thr <= 0: number of v <= w pairs to keep */
+  int spin;                /* 0 singlet (K1e factor 2, Eq. k1e), 1 triplet (factor 0) */
+} bse_system;
+
+/* Create a context: validates the system, uploads it, computes psi_v(r).
+ * stream: a cudaStream_t (NULL = legacy default stream). Device = current device. */
+int bse_create(const bse_system* sys, int precision, void* stream, bse_ctx** out);
+
+/* Overlaps O_vw (Eq. overlap, FP64 grid quadrature), the pair rule, and the screened
+ * integrals tau_vw = W[psi_v psi_w] for every kept pair v <= w (Eqs. tau,
+ * tau_from_tau_u, pdep). Pair rule: keep iff O_vw >= thr; with keep_pairs the
+ * threshold is the midpoint of the gap between the k-th and (k+1)-th largest
+ * off-diagonal overlaps (k = keep_pairs - n_occ), moved to the nearest gap of at
+ * least 1e-9 of its midpoint, checked at k+1, k-1, k+2, k-2, ...; diagonal pairs
+ * are always kept. Outputs (nullable): number of kept v <= w pairs, threshold. */
+int bse_build_tau(bse_ctx* ctx, int64_t* n_pairs_out, double* thr_out);
+
+/* Kept pairs in row-major (v, w), v <= w order; host arrays of length n_pairs. */
+int bse_get_pairs(const bse_ctx* ctx, int32_t* v_out, int32_t* w_out);
+
+/* Overlap matrix O (host [n_occ][n_occ], FP64), available after bse_build_tau. */
+int bse_get_overlaps(const bse_ctx* ctx, double* o_out);
+
+/* R = P_c (D + K1e - K1d) A for a block of n_vec trial vectors (Eqs. evp, d, k1e, k1d).
+ * a_in, a_out: DEVICE pointers [n_vec][n_occ][n_pw], double for BSE_PREC_FP64 and
+ * float for BSE_PREC_MIXED. a_in must lie in the conduction space (P_c a = a) with
+ * zero pad entries; a_out must not alias a_in. Requires bse_build_tau first. */
+int bse_apply_liouville(bse_ctx* ctx, int n_vec, const void* a_in, void* a_out);
+
+typedef struct {
+  int n_eig;        /* number of lowest excitations wanted */
+  int block;        /* trial vectors added per iteration (also the initial count) */
+  int max_sub;      /* maximum subspace size; restart keeps 2*n_eig Ritz vectors */
+  int max_it;       /* iteration limit */
+  double res_tol;   /* converged when every ||L x - theta x||_2 <= res_tol (Ha) */
+  int precond;      /* 0 diagonal, 1 learned (falls back to diagonal if no net loaded) */
+} bse_davidson_opts;
+
+typedef struct {
+  int iterations;
+  int n_apply;          /* trial vectors passed through the operator */
+  double ms_total;      /* wall time of the call (CUDA events on the context stream) */
+  double ms_apply;      /* of which operator applications */
+  double res_max;       /* largest residual norm at exit */
+  int precond_fallbacks;/* learned corrections replaced by the diagonal ones */
+} bse_davidson_stats;
+
+/* Lowest n_eig eigenpairs of the Liouville operator (Eq. evp) by block Davidson.
+ * omega_out: host [n_eig] (Ha), ascending. vec_out (nullable): DEVICE
+ * [n_eig][n_occ][n_pw] in the context precision. stats (nullable).
+ * On BSE_ERR_NOT_CONVERGED omega_out, vec_out and stats hold the last Ritz pairs. */
+int bse_davidson(bse_ctx* ctx, const bse_davidson_opts* opts, double* omega_out,
+                 void* vec_out, bse_davidson_stats* stats);
+
+/* Human-readable description of the last error on this context (never NULL). */
+const char* bse_last_error(const bse_ctx* ctx);
+
+/* Library build string (compile flags, arch). */
+const char* bse_version(void);
+
+void bse_destroy(bse_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSE_H_ */

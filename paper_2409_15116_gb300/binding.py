@@ -1,0 +1,194 @@
+"""Thin ctypes binding of the C ABI declared in include/bse.h (argument marshalling only).
+
+Every step of the hot path runs in the CUDA library; this module converts host arrays
+to the ``bse_system`` struct, passes device pointers of torch tensors, and raises on
+non-zero status codes. It fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libbse.so")
+
+BSE_OK = 0
+BSE_ERR_NOT_CONVERGED = -5
+STATUS = {0: "BSE_OK", -1: "BSE_ERR_INVALID_ARG", -2: "BSE_ERR_CUDA", -3: "BSE_ERR_OOM",
+          -4: "BSE_ERR_NUMERIC", -5: "BSE_ERR_NOT_CONVERGED", -6: "BSE_ERR_TIMEOUT",
+          -7: "BSE_ERR_STATE"}
+PREC_FP64, PREC_MIXED = 0, 1
+
+# every symbol include/bse.h declares
+EXPORTS = ["bse_create", "bse_build_tau", "bse_get_pairs", "bse_get_overlaps",
+           "bse_apply_liouville", "bse_davidson", "bse_last_error", "bse_version",
+           "bse_destroy"]
+
+
+class BseError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class System(C.Structure):
+    _fields_ = [("n_grid", C.c_int), ("L", C.c_double), ("n_half", C.c_int),
+                ("miller", C.POINTER(C.c_int32)), ("n_occ", C.c_int),
+                ("psi", C.POINTER(C.c_double)), ("eps", C.POINTER(C.c_double)),
+                ("v_loc", C.POINTER(C.c_double)), ("scissor", C.c_double),
+                ("n_pdep", C.c_int), ("pdep", C.POINTER(C.c_double)),
+                ("lam", C.POINTER(C.c_double)), ("overlap_thr", C.c_double),
+                ("keep_pairs", C.c_int64), ("spin", C.c_int)]
+
+
+class DavidsonOpts(C.Structure):
+    _fields_ = [("n_eig", C.c_int), ("block", C.c_int), ("max_sub", C.c_int),
+                ("max_it", C.c_int), ("res_tol", C.c_double), ("precond", C.c_int)]
+
+
+class DavidsonStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("n_apply", C.c_int), ("ms_total", C.c_double),
+                ("ms_apply", C.c_double), ("res_max", C.c_double),
+                ("precond_fallbacks", C.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libbse.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with paper_2409_15116_gb300.build.build()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.bse_create.argtypes = [C.POINTER(System), C.c_int, P, C.POINTER(P)]
+    lib.bse_build_tau.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+    lib.bse_get_pairs.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.bse_get_overlaps.argtypes = [P, C.POINTER(C.c_double)]
+    lib.bse_apply_liouville.argtypes = [P, C.c_int, P, P]
+    lib.bse_davidson.argtypes = [P, C.POINTER(DavidsonOpts), C.POINTER(C.c_double), P,
+                                 C.POINTER(DavidsonStats)]
+    lib.bse_last_error.argtypes = [P]
+    lib.bse_last_error.restype = C.c_char_p
+    lib.bse_version.restype = C.c_char_p
+    lib.bse_destroy.argtypes = [P]
+    lib.bse_destroy.restype = None
+    for name in EXPORTS:
+        getattr(lib, name)
+    _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+@dataclass
+class Stats:
+    iterations: int
+    n_apply: int
+    ms_total: float
+    ms_apply: float
+    res_max: float
+    precond_fallbacks: int
+
+
+class Context:
+    """One system on the current CUDA device; ``sys`` is any object with the instance fields
+    (L, n_grid, miller, psi, eps, v_loc, scissor, pdep, lam, overlap_thr, keep_pairs, spin)."""
+
+    def __init__(self, sys, precision: int = PREC_FP64, stream=None):
+        self.lib = load()
+        self.precision = precision
+        self._keep = []
+        miller = np.ascontiguousarray(sys.miller, dtype=np.int32)
+        psi = np.ascontiguousarray(sys.psi, dtype=np.float64)
+        eps = np.ascontiguousarray(sys.eps, dtype=np.float64)
+        vloc = np.ascontiguousarray(sys.v_loc, dtype=np.float64)
+        pdep = np.ascontiguousarray(sys.pdep, dtype=np.float64)
+        lam = np.ascontiguousarray(sys.lam, dtype=np.float64)
+        self._keep += [miller, psi, eps, vloc, pdep, lam]
+        s = System(n_grid=int(sys.n_grid), L=float(sys.L), n_half=int(miller.shape[0]),
+                   miller=miller.ctypes.data_as(C.POINTER(C.c_int32)), n_occ=int(psi.shape[0]),
+                   psi=_dptr(psi), eps=_dptr(eps), v_loc=_dptr(vloc), scissor=float(sys.scissor),
+                   n_pdep=int(pdep.shape[0]), pdep=_dptr(pdep), lam=_dptr(lam),
+                   overlap_thr=float(sys.overlap_thr), keep_pairs=int(sys.keep_pairs),
+                   spin=int(sys.spin))
+        self.n_occ, self.n_pw = psi.shape
+        h = C.c_void_p()
+        st = C.c_void_p(int(stream) if stream is not None else 0)
+        rc = self.lib.bse_create(C.byref(s), precision, st, C.byref(h))
+        self.h = h
+        if rc != BSE_OK:
+            msg = self.lib.bse_last_error(h).decode() if h else "bse_create failed"
+            if h:
+                self.lib.bse_destroy(h)
+                self.h = C.c_void_p()
+            raise BseError(rc, msg)
+
+    def _check(self, rc):
+        if rc != BSE_OK:
+            raise BseError(rc, self.lib.bse_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            self.lib.bse_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_tau(self):
+        n = C.c_int64()
+        t = C.c_double()
+        self._check(self.lib.bse_build_tau(self.h, C.byref(n), C.byref(t)))
+        self.n_pairs = int(n.value)
+        return self.n_pairs, float(t.value)
+
+    def pairs(self):
+        v = np.zeros(self.n_pairs, np.int32)
+        w = np.zeros(self.n_pairs, np.int32)
+        self._check(self.lib.bse_get_pairs(self.h, v.ctypes.data_as(C.POINTER(C.c_int32)),
+                                           w.ctypes.data_as(C.POINTER(C.c_int32))))
+        return np.stack([v, w], 1)
+
+    def overlaps(self):
+        o = np.zeros((self.n_occ, self.n_occ))
+        self._check(self.lib.bse_get_overlaps(self.h, _dptr(o)))
+        return o
+
+    def apply(self, a_in, a_out):
+        """a_in, a_out: contiguous CUDA tensors [n_vec, n_occ, n_pw] (float64 or float32)."""
+        assert a_in.is_contiguous() and a_out.is_contiguous()
+        assert tuple(a_in.shape[1:]) == (self.n_occ, self.n_pw) and a_in.shape == a_out.shape
+        self._check(self.lib.bse_apply_liouville(self.h, int(a_in.shape[0]),
+                                                 C.c_void_p(a_in.data_ptr()),
+                                                 C.c_void_p(a_out.data_ptr())))
+        return a_out
+
+    def davidson(self, n_eig, block, max_sub, max_it=200, res_tol=1e-5, precond=0, vec_out=None,
+                 allow_not_converged=False):
+        opts = DavidsonOpts(n_eig=n_eig, block=block, max_sub=max_sub, max_it=max_it,
+                            res_tol=res_tol, precond=precond)
+        om = np.zeros(n_eig)
+        st = DavidsonStats()
+        vp = C.c_void_p(vec_out.data_ptr()) if vec_out is not None else C.c_void_p()
+        rc = self.lib.bse_davidson(self.h, C.byref(opts), _dptr(om), vp, C.byref(st))
+        if not (rc == BSE_OK or (allow_not_converged and rc == BSE_ERR_NOT_CONVERGED)):
+            self._check(rc)
+        stats = Stats(st.iterations, st.n_apply, st.ms_total, st.ms_apply, st.res_max,
+                      st.precond_fallbacks)
+        return om, stats
+
+
+def version() -> str:
+    return load().bse_version().decode()

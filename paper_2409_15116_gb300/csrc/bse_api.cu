@@ -1,0 +1,743 @@
+// C ABI of the BSE hot path: context set-up, screened-integral build, Liouville
+// operator application and block Davidson (declared in include/bse.h).
+#include "bse.h"
+#include "kernels.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <queue>
+#include <string>
+#include <vector>
+
+using namespace bse;
+
+struct bse_ctx {
+  // problem
+  int N = 0;
+  long n3 = 0;
+  double L = 0, omega = 0, scissor = 0, thr_in = 0, v0 = 0;
+  int n_half = 0, n_pw = 0, n_occ = 0, n_pdep = 0, spin = 0, prec = 0;
+  int64_t keep_pairs = 0;
+  cudaStream_t st = nullptr;
+  std::string err = "no error";
+  std::vector<double> g2p_h, eps_h, O_h;
+  std::vector<int32_t> pv_h, pw_h;
+  double thr = 0;
+  bool tau_ready = false;
+  // device, common
+  int *gpos = nullptr, *gneg = nullptr;
+  double *g2p = nullptr, *eps = nullptr, *f = nullptr;
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+  // FP64 masters and FP32 copies
+  double *psi64 = nullptr, *pdep64 = nullptr, *vloc64 = nullptr, *upsi64 = nullptr;
+  float *psi32 = nullptr, *pdep32 = nullptr, *vloc32 = nullptr, *upsi32 = nullptr;
+  // pairs / tau
+  int *nbr_ptr = nullptr, *nbr_w = nullptr, *nbr_p = nullptr, *pv = nullptr, *pw = nullptr;
+  int64_t n_pairs = 0;
+  void* tau = nullptr;
+  // operator workspace
+  void *ws_a = nullptr, *ws_r = nullptr, *ws_h = nullptr, *ws_c = nullptr;
+  long ws_vecs = 0;
+  size_t ws_budget = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+int fail(bse_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+int cuda_fail(bse_ctx* c, cudaError_t e, const char* what) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  if (c) c->err = buf;
+  return (e == cudaErrorMemoryAllocation) ? BSE_ERR_OOM : BSE_ERR_CUDA;
+}
+#define CK(call)                                             \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
+    if (_e != cudaSuccess) return cuda_fail(c, _e, #call);   \
+  } while (0)
+
+template <typename T>
+int dalloc(bse_ctx* c, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char buf[256];
+    snprintf(buf, sizeof(buf), "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+             cudaGetErrorString(e));
+    c->err = buf;
+    return BSE_ERR_OOM;
+  }
+  c->allocs.push_back(*p);
+  return BSE_OK;
+}
+void dfree(bse_ctx* c, void* p) {
+  if (!p) return;
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+  if (it != c->allocs.end()) c->allocs.erase(it);
+  cudaFree(p);
+}
+#define CA(expr)                    \
+  do {                              \
+    int _r = (expr);                \
+    if (_r != BSE_OK) return _r;    \
+  } while (0)
+
+bool all_finite(const double* x, long n) { return finite_check_host(x, n); }
+
+// threshold rule of the pair list (same reading as documented in bse.h)
+double choose_threshold(const std::vector<double>& O, int n, double thr, int64_t keep) {
+  if (thr > 0) return thr;
+  std::vector<double> off;
+  off.reserve((size_t)n * (n - 1) / 2);
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) off.push_back(O[(size_t)i * n + j]);
+  std::sort(off.begin(), off.end(), std::greater<double>());
+  const long k = (long)keep - n;
+  if (k <= 0) return 0.5 * ((off.empty() ? 0.0 : off[0]) + 1.0);
+  if (k >= (long)off.size()) return 0.0;
+  auto ok = [&](long j) {
+    if (j < 1 || j >= (long)off.size()) return false;
+    const double gap = off[j - 1] - off[j];
+    return gap >= 1e-9 * 0.5 * (off[j - 1] + off[j]) && gap > 0;
+  };
+  long j = k;
+  if (!ok(j)) {
+    for (long d = 1; d < (long)off.size(); ++d) {
+      if (ok(k + d)) { j = k + d; break; }
+      if (ok(k - d)) { j = k - d; break; }
+    }
+  }
+  return 0.5 * (off[j - 1] + off[j]);
+}
+
+template <typename T> T* upsi_of(bse_ctx* c);
+template <> double* upsi_of<double>(bse_ctx* c) { return c->upsi64; }
+template <> float* upsi_of<float>(bse_ctx* c) { return c->upsi32; }
+template <typename T> T* psi_of(bse_ctx* c);
+template <> double* psi_of<double>(bse_ctx* c) { return c->psi64; }
+template <> float* psi_of<float>(bse_ctx* c) { return c->psi32; }
+template <typename T> T* pdep_of(bse_ctx* c);
+template <> double* pdep_of<double>(bse_ctx* c) { return c->pdep64; }
+template <> float* pdep_of<float>(bse_ctx* c) { return c->pdep32; }
+template <typename T> T* vloc_of(bse_ctx* c);
+template <> double* vloc_of<double>(bse_ctx* c) { return c->vloc64; }
+template <> float* vloc_of<float>(bse_ctx* c) { return c->vloc32; }
+template <typename T> const cplx<T>* tw_of(bse_ctx* c);
+template <> const double2* tw_of<double>(bse_ctx* c) { return c->tw64; }
+template <> const float2* tw_of<float>(bse_ctx* c) { return c->tw32; }
+
+// ---------------------------------------------------------------------------------
+// P_c = 1 - sum_v |psi_v><psi_v| on `rows` packed orbital rows (Section 2)
+// ---------------------------------------------------------------------------------
+template <typename T>
+int project(bse_ctx* c, long rows, T* X, T* cbuf) {
+  if (rows <= 0) return BSE_OK;
+  const T* psi = psi_of<T>(c);
+  // cbuf [rows x n_occ] = X psi^T ; X -= cbuf psi
+  CK((gemm<T, T>(false, true, (int)rows, c->n_occ, c->n_pw, 1.0, X, c->n_pw, psi, c->n_pw, 0.0,
+                 cbuf, c->n_occ, 1, c->st)));
+  CK((gemm<T, T>(false, false, (int)rows, c->n_pw, c->n_occ, -1.0, cbuf, c->n_occ, psi, c->n_pw,
+                 1.0, X, c->n_pw, 1, c->st)));
+  CK(zero_pad_column<T>((int)rows, c->n_pw, X, c->st));
+  return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// operator workspace
+// ---------------------------------------------------------------------------------
+template <typename T>
+int ensure_workspace(bse_ctx* c, long n_vec) {
+  const size_t per_vec = (size_t)2 * ((c->n_occ + 1) / 2) * c->n3 * sizeof(cplx<T>);
+  long cap = (long)std::max<size_t>(1, c->ws_budget / std::max<size_t>(1, per_vec));
+  long want = std::min(n_vec, cap);
+  if (want <= c->ws_vecs) return BSE_OK;
+  dfree(c, c->ws_a); dfree(c, c->ws_r); dfree(c, c->ws_h); dfree(c, c->ws_c);
+  c->ws_a = c->ws_r = c->ws_h = c->ws_c = nullptr;
+  c->ws_vecs = 0;
+  const long nf = want * c->n_occ;
+  const long ngr = (nf + 1) / 2;
+  cplx<T>* p;
+  CA(dalloc(c, &p, (size_t)ngr * c->n3)); c->ws_a = p;
+  CA(dalloc(c, &p, (size_t)ngr * c->n3)); c->ws_r = p;
+  CA(dalloc(c, &p, (size_t)((want + 1) / 2) * c->n3)); c->ws_h = p;
+  T* q;
+  CA(dalloc(c, &q, (size_t)nf * c->n_occ)); c->ws_c = q;
+  c->ws_vecs = want;
+  return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// R = P_c (D + K1e - K1d) A   (Eqs. evp, d, k1e, k1d)
+// ---------------------------------------------------------------------------------
+template <typename T>
+int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
+  if (n_vec <= 0) return BSE_OK;
+  CA(ensure_workspace<T>(c, n_vec));
+  const long chunk = c->ws_vecs;
+  const int N = c->N;
+  const long n3 = c->n3;
+  const T* tau = (const T*)c->tau;
+  const double sf = (c->spin == 0) ? 2.0 : 0.0;
+  for (long s0 = 0; s0 < n_vec; s0 += chunk) {
+    const long nv = std::min(chunk, n_vec - s0);
+    const long nf = nv * c->n_occ;
+    const long ngr = (nf + 1) / 2;
+    const T* ain = a_in + s0 * c->n_occ * c->n_pw;
+    T* aout = a_out + s0 * c->n_occ * c->n_pw;
+    cplx<T>* ga = (cplx<T>*)c->ws_a;
+    cplx<T>* gr = (cplx<T>*)c->ws_r;
+    cplx<T>* gh = (cplx<T>*)c->ws_h;
+    // a_sv(G) -> a_sv(r)
+    CK((sphere_unpack<T, T>(ain, nf, c->n_pw, c->n_half, c->gpos, c->gneg, ga, n3, true, false, c->st)));
+    CK(fft3d<T>(ga, ngr, N, +1, tw_of<T>(c), c->st));
+    // Hartree potential of the pair density sum_w psi_w a_sw (Eq. k1e)
+    const long nh = (nv + 1) / 2;
+    CK(cudaMemsetAsync(gh, 0, (size_t)nh * n3 * sizeof(cplx<T>), c->st));
+    if (sf != 0.0) {
+      CK(hartree_density<T>((int)nv, c->n_occ, n3, (const T*)ga, upsi_of<T>(c), (T*)gh, c->st));
+      CK(fft3d<T>(gh, nh, N, -1, tw_of<T>(c), c->st));
+      CK(grid_coulomb<T>(gh, nh, N, c->L, c->omega, 0, 1.0 / (double)n3, c->st));
+      CK(fft3d<T>(gh, nh, N, +1, tw_of<T>(c), c->st));
+    }
+    // real-space combination with the screened direct term (Eq. k1d)
+    if (nf & 1) CK(cudaMemsetAsync(gr + (ngr - 1) * n3, 0, (size_t)n3 * sizeof(cplx<T>), c->st));
+    CK(k1d_combine<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->nbr_ptr, c->nbr_w, c->nbr_p,
+                      vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
+    // back to the sphere, plus (1/2|G|^2 + Delta - eps_v) a (Eq. d)
+    CK(fft3d<T>(gr, ngr, N, -1, tw_of<T>(c), c->st));
+    CK((sphere_pack<T, T>(gr, nf, c->n_pw, c->n_half, c->gpos, c->gneg, n3, 1.0 / (double)n3, aout,
+                          ain, c->g2p, c->eps, c->scissor, c->n_occ, c->st)));
+    CA(project<T>(c, nf, aout, (T*)c->ws_c));
+  }
+  return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// overlaps, pair rule and screened integrals (Eqs. overlap, tau, tau_from_tau_u, pdep)
+// ---------------------------------------------------------------------------------
+template <typename T>
+int build_tau_impl(bse_ctx* c) {
+  const long n3 = c->n3;
+  const int n = c->n_occ;
+  // O_vw in FP64 always, so that the lists do not depend on the precision mode
+  {
+    double *rho, *gram, *dg;
+    CA(dalloc(c, &rho, (size_t)n * n3));
+    CA(dalloc(c, &gram, (size_t)n * n));
+    CA(dalloc(c, &dg, (size_t)n));
+    CK(square_fields(n, c->upsi64, n3, rho, c->st));
+    CK((gemm<double, double>(false, true, n, n, (int)n3, 1.0, rho, n3, rho, n3, 0.0, gram, n, 0, c->st)));
+    CK(normalize_overlap(n, gram, dg, c->st));
+    c->O_h.assign((size_t)n * n, 0.0);
+    CK(cudaMemcpyAsync(c->O_h.data(), gram, sizeof(double) * n * n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    dfree(c, rho); dfree(c, gram); dfree(c, dg);
+  }
+  if (!all_finite(c->O_h.data(), (long)n * n)) return fail(c, BSE_ERR_NUMERIC, "non-finite overlap");
+  c->thr = choose_threshold(c->O_h, n, c->thr_in, c->keep_pairs);
+  // pair list v <= w (row-major) and CSR neighbour lists in both directions
+  std::vector<std::vector<int>> pid(n, std::vector<int>(n, -1));
+  c->pv_h.clear(); c->pw_h.clear();
+  for (int v = 0; v < n; ++v)
+    for (int w = v; w < n; ++w) {
+      const bool keep = (v == w) || (c->O_h[(size_t)v * n + w] >= c->thr);
+      if (keep) {
+        pid[v][w] = pid[w][v] = (int)c->pv_h.size();
+        c->pv_h.push_back(v); c->pw_h.push_back(w);
+      }
+    }
+  c->n_pairs = (int64_t)c->pv_h.size();
+  std::vector<int> ptr(n + 1, 0), nw, np;
+  for (int v = 0; v < n; ++v) {
+    for (int w = 0; w < n; ++w)
+      if (pid[v][w] >= 0) { nw.push_back(w); np.push_back(pid[v][w]); }
+    ptr[v + 1] = (int)nw.size();
+  }
+  dfree(c, c->nbr_ptr); dfree(c, c->nbr_w); dfree(c, c->nbr_p); dfree(c, c->pv); dfree(c, c->pw);
+  dfree(c, c->tau); c->tau = nullptr;
+  CA(dalloc(c, &c->nbr_ptr, ptr.size()));
+  CA(dalloc(c, &c->nbr_w, nw.size()));
+  CA(dalloc(c, &c->nbr_p, np.size()));
+  CA(dalloc(c, &c->pv, c->pv_h.size()));
+  CA(dalloc(c, &c->pw, c->pw_h.size()));
+  CK(cudaMemcpyAsync(c->nbr_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->nbr_w, nw.data(), sizeof(int) * nw.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->nbr_p, np.data(), sizeof(int) * np.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->pv, c->pv_h.data(), sizeof(int) * c->pv_h.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->pw, c->pw_h.data(), sizeof(int) * c->pw_h.size(), cudaMemcpyHostToDevice, c->st));
+  // tau_vw = v^{1/2} (1 + chi_bar) v^{1/2} (psi_v psi_w), batched over pairs
+  T* tau;
+  CA(dalloc(c, &tau, (size_t)c->n_pairs * n3));
+  c->tau = tau;
+  const size_t budget = (size_t)2 << 30;
+  long nb = (long)(budget / (n3 * sizeof(cplx<T>))) * 2;
+  nb = std::max<long>(2, std::min<long>(nb, 4096));
+  nb = std::min<long>(nb, (c->n_pairs + 1) / 2 * 2);
+  cplx<T>* grids;
+  T *X, *X2, *Cp;
+  CA(dalloc(c, &grids, (size_t)((nb + 1) / 2) * n3));
+  CA(dalloc(c, &X, (size_t)nb * c->n_pw));
+  CA(dalloc(c, &X2, (size_t)nb * c->n_pw));
+  CA(dalloc(c, &Cp, (size_t)nb * std::max(1, c->n_pdep)));
+  const T* pd = pdep_of<T>(c);
+  for (long p0 = 0; p0 < c->n_pairs; p0 += nb) {
+    const int b = (int)std::min<long>(nb, c->n_pairs - p0);
+    const long ng = (b + 1) / 2;
+    CK(pair_product<T>(b, c->pv + p0, c->pw + p0, upsi_of<T>(c), n3, 1.0 / c->omega, grids, c->st));
+    CK(fft3d<T>(grids, ng, c->N, -1, tw_of<T>(c), c->st));
+    CK(grid_coulomb<T>(grids, ng, c->N, c->L, c->omega, 1, 1.0 / (double)n3, c->st));
+    if (c->n_pdep > 0) {
+      CK((sphere_pack<T, T>(grids, b, c->n_pw, c->n_half, c->gpos, c->gneg, n3, 1.0, X, nullptr,
+                            nullptr, nullptr, 0.0, 1, c->st)));
+      CK((gemm<T, T>(false, true, b, c->n_pdep, c->n_pw, 1.0, X, c->n_pw, pd, c->n_pw, 0.0, Cp,
+                     c->n_pdep, 1, c->st)));
+      CK(scale_columns<T>(b, c->n_pdep, Cp, c->n_pdep, c->f, c->st));
+      CK((gemm<T, T>(false, false, b, c->n_pw, c->n_pdep, 1.0, Cp, c->n_pdep, pd, c->n_pw, 0.0, X2,
+                     c->n_pw, 1, c->st)));
+      CK((sphere_unpack<T, T>(X2, b, c->n_pw, c->n_half, c->gpos, c->gneg, grids, n3, false, true, c->st)));
+    }
+    CK(grid_coulomb<T>(grids, ng, c->N, c->L, c->omega, 1, 1.0, c->st));
+    CK(fft3d<T>(grids, ng, c->N, +1, tw_of<T>(c), c->st));
+    CK(deinterleave_pairs<T>(b, grids, n3, tau + p0 * n3, c->st));
+  }
+  CK(cudaStreamSynchronize(c->st));
+  dfree(c, grids); dfree(c, X); dfree(c, X2); dfree(c, Cp);
+  c->tau_ready = true;
+  return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// block Davidson (Section 3); algebra in FP64 (Gram / Rayleigh-Ritz accumulate in
+// FP64, Jacobi eigensolver and Cholesky in FP64), vectors in the context precision
+// ---------------------------------------------------------------------------------
+struct Cand { double d; long flat; };
+
+template <typename T>
+int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* vec_out,
+                  bse_davidson_stats* stats) {
+  using clk = std::chrono::steady_clock;
+  const auto t_start = clk::now();
+  const int ne = o->n_eig, b = o->block, ms = o->max_sub;
+  const long dim = (long)c->n_occ * c->n_pw;
+  if (ne < 1 || b < 1 || ms < 2 * ne + b || ms > 160 || b > 128 || o->max_it < 1 || !(o->res_tol > 0))
+    return fail(c, BSE_ERR_INVALID_ARG, "davidson options: need n_eig>=1, 1<=block<=128, 2*n_eig+block<=max_sub<=160, max_it>=1, res_tol>0");
+  if ((long)ne > dim) return fail(c, BSE_ERR_INVALID_ARG, "n_eig exceeds the problem dimension");
+  const int keep = 2 * ne;
+  std::vector<void*> mine;
+  auto al = [&](auto** p, size_t n) {
+    int r = dalloc(c, p, n);
+    if (r == BSE_OK) mine.push_back(*p);
+    return r;
+  };
+  struct Guard {
+    bse_ctx* c; std::vector<void*>* m;
+    ~Guard() { for (void* p : *m) dfree(c, p); }
+  } guard{c, &mine};
+  T *V, *W, *X, *LX, *Rr, *Tt, *Tt2, *S1, *S2, *Yt, *Cmt, *Lt;
+  double *Hs, *Yv, *jw, *theta, *nrm, *Cm, *Sg, *Linv;
+  int *info, *which;
+  CA(al(&V, (size_t)ms * dim)); CA(al(&W, (size_t)ms * dim));
+  CA(al(&X, (size_t)ne * dim)); CA(al(&LX, (size_t)ne * dim)); CA(al(&Rr, (size_t)ne * dim));
+  CA(al(&Tt, (size_t)b * dim)); CA(al(&Tt2, (size_t)b * dim));
+  CA(al(&S1, (size_t)keep * dim)); CA(al(&S2, (size_t)keep * dim));
+  CA(al(&Yt, (size_t)ms * ms)); CA(al(&Cmt, (size_t)ms * b)); CA(al(&Lt, (size_t)b * b));
+  CA(al(&Hs, (size_t)ms * ms)); CA(al(&Yv, (size_t)ms * ms)); CA(al(&jw, (size_t)ms * ms));
+  CA(al(&theta, (size_t)ms)); CA(al(&nrm, (size_t)ms)); CA(al(&Cm, (size_t)ms * b));
+  CA(al(&Sg, (size_t)b * b)); CA(al(&Linv, (size_t)b * b));
+  CA(al(&info, 4)); CA(al(&which, (size_t)b));
+  T* pcbuf = nullptr;
+  CA(al(&pcbuf, (size_t)b * c->n_occ * c->n_occ + 16));
+  double ms_apply = 0;
+  int n_apply = 0;
+  auto timed_apply = [&](long nv, const T* in, T* out) -> int {
+    CK(cudaStreamSynchronize(c->st));
+    const auto t0 = clk::now();
+    int r = apply_impl<T>(c, nv, in, out);
+    if (r != BSE_OK) return r;
+    CK(cudaStreamSynchronize(c->st));
+    ms_apply += std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    n_apply += (int)nv;
+    return BSE_OK;
+  };
+  auto proj = [&](long nvec, T* Xp) -> int {
+    // P_c row by row in chunks of `b` vectors (cbuf holds b * n_occ x n_occ)
+    for (long i = 0; i < nvec; i += b) {
+      const long k = std::min<long>(b, nvec - i);
+      CA(project<T>(c, k * c->n_occ, Xp + i * dim, pcbuf));
+    }
+    return BSE_OK;
+  };
+  // ---- initial guess: unit vectors at the lowest diagonal entries ----
+  std::vector<int> order(c->n_occ);
+  for (int v = 0; v < c->n_occ; ++v) order[v] = v;
+  auto dval = [&](int v, int j) { return 0.5 * c->g2p_h[j] + c->v0 + c->scissor - c->eps_h[v]; };
+  // merge of the per-orbital lists (g2p_h is non-decreasing in j apart from the pad j = 1)
+  std::vector<std::vector<int>> jord(1);
+  {
+    std::vector<int> js(c->n_pw);
+    for (int j = 0; j < c->n_pw; ++j) js[j] = j;
+    std::stable_sort(js.begin(), js.end(), [&](int a, int bb) { return c->g2p_h[a] < c->g2p_h[bb]; });
+    jord[0] = js;
+  }
+  auto cmp = [](const std::pair<Cand, int>& a, const std::pair<Cand, int>& bb) {
+    if (a.first.d != bb.first.d) return a.first.d > bb.first.d;
+    return a.first.flat > bb.first.flat;
+  };
+  std::priority_queue<std::pair<Cand, int>, std::vector<std::pair<Cand, int>>, decltype(cmp)> pq(cmp);
+  std::vector<int> pos(c->n_occ, 0);
+  // ties within one orbital's list must come out in flat-index order: re-sort equal-d runs
+  {
+    auto& js = jord[0];
+    std::stable_sort(js.begin(), js.end(), [&](int a, int bb) {
+      if (c->g2p_h[a] != c->g2p_h[bb]) return c->g2p_h[a] < c->g2p_h[bb];
+      return a < bb;
+    });
+  }
+  for (int v = 0; v < c->n_occ; ++v) {
+    const int j = jord[0][0];
+    pq.push({Cand{dval(v, j), (long)v * c->n_pw + j}, v});
+  }
+  int m = 0;
+  std::vector<double> hn(std::max(ms, b));
+  while (m < b && !pq.empty()) {
+    auto top = pq.top(); pq.pop();
+    const int v = top.second;
+    if (++pos[v] < c->n_pw) {
+      const int j = jord[0][pos[v]];
+      pq.push({Cand{dval(v, j), (long)v * c->n_pw + j}, v});
+    }
+    T* x = V + (long)m * dim;
+    CK(set_unit<T>(x, dim, top.first.flat, c->st));
+    CA(project<T>(c, c->n_occ, x, pcbuf));
+    for (int pass = 0; pass < 2 && m > 0; ++pass) {
+      CK((gemm<T, double>(false, true, m, 1, (int)dim, 1.0, V, dim, x, dim, 0.0, Cm, 1, 0, c->st)));
+      CK((convert<double, T>(m, Cm, Cmt, c->st)));
+      CK((gemm<T, T>(true, false, 1, (int)dim, m, -1.0, Cmt, 1, V, dim, 1.0, x, dim, 1, c->st)));
+    }
+    CK(row_norms2<T>(1, dim, x, nrm, c->st));
+    double n2 = 0;
+    CK(cudaMemcpyAsync(&n2, nrm, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (std::sqrt(n2) > 0.1) {
+      const double s = 1.0 / std::sqrt(n2);
+      CK(cudaMemcpyAsync(nrm, &s, sizeof(double), cudaMemcpyHostToDevice, c->st));
+      CK(scale_rows<T>(1, dim, x, nrm, c->st));
+      ++m;
+    }
+  }
+  if (m == 0) return fail(c, BSE_ERR_NUMERIC, "no initial vector survives the projection");
+  CA(timed_apply(m, V, W));
+  int it = 0;
+  bool converged = false;
+  std::vector<double> th(ms), rn(ms);
+  int kk = 0;
+  while (true) {
+    ++it;
+    CK((gemm<T, double>(false, true, m, m, (int)dim, 1.0, V, dim, W, dim, 0.0, Hs, m, 0, c->st)));
+    CK(symmetrize(m, Hs, m, c->st));
+    CK(jacobi_eigh(m, Hs, m, jw, Yv, theta, info, c->st));
+    kk = std::min(ne, m);
+    CK((convert<double, T>((long)m * m, Yv, Yt, c->st)));
+    CK((gemm<T, T>(true, false, kk, (int)dim, m, 1.0, Yt, m, V, dim, 0.0, X, dim, 1, c->st)));
+    CK((gemm<T, T>(true, false, kk, (int)dim, m, 1.0, Yt, m, W, dim, 0.0, LX, dim, 1, c->st)));
+    CK(residuals<T>(kk, dim, X, LX, theta, Rr, nrm, c->st));
+    CK(cudaMemcpyAsync(th.data(), theta, sizeof(double) * kk, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(rn.data(), nrm, sizeof(double) * kk, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (!all_finite(th.data(), kk) || !all_finite(rn.data(), kk))
+      return fail(c, BSE_ERR_NUMERIC, "non-finite Ritz value or residual");
+    std::vector<int> todo;
+    for (int i = 0; i < kk; ++i) {
+      rn[i] = std::sqrt(rn[i]);
+      if (rn[i] > o->res_tol && (int)todo.size() < b) todo.push_back(i);
+    }
+    if (kk == ne && todo.empty()) { converged = true; break; }
+    if (it >= o->max_it) break;
+    int nt = (int)todo.size();
+    if (nt == 0) break;
+    CK(cudaMemcpyAsync(which, todo.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, c->st));
+    CK(precond_diag<T>(nt, c->n_occ, c->n_pw, Rr, theta, which, c->g2p, c->eps, c->v0, c->scissor,
+                       Tt, c->st));
+    CA(proj(nt, Tt));
+    if (m + nt > ms) {
+      const int kp = std::min(keep, m);
+      CK((gemm<T, T>(true, false, kp, (int)dim, m, 1.0, Yt, m, V, dim, 0.0, S1, dim, 1, c->st)));
+      CK((gemm<T, T>(true, false, kp, (int)dim, m, 1.0, Yt, m, W, dim, 0.0, S2, dim, 1, c->st)));
+      CK(cudaMemcpyAsync(V, S1, sizeof(T) * kp * dim, cudaMemcpyDeviceToDevice, c->st));
+      CK(cudaMemcpyAsync(W, S2, sizeof(T) * kp * dim, cudaMemcpyDeviceToDevice, c->st));
+      m = kp;
+    }
+    // CGS2 against V, dropping directions that lose all but 1e-8 of their norm
+    std::vector<double> n0(nt), n1(nt);
+    CK(row_norms2<T>(nt, dim, Tt, nrm, c->st));
+    CK(cudaMemcpyAsync(n0.data(), nrm, sizeof(double) * nt, cudaMemcpyDeviceToHost, c->st));
+    for (int pass = 0; pass < 2; ++pass) {
+      CK((gemm<T, double>(false, true, m, nt, (int)dim, 1.0, V, dim, Tt, dim, 0.0, Cm, nt, 0, c->st)));
+      CK((convert<double, T>((long)m * nt, Cm, Cmt, c->st)));
+      CK((gemm<T, T>(true, false, nt, (int)dim, m, -1.0, Cmt, nt, V, dim, 1.0, Tt, dim, 1, c->st)));
+    }
+    CK(row_norms2<T>(nt, dim, Tt, nrm, c->st));
+    CK(cudaMemcpyAsync(n1.data(), nrm, sizeof(double) * nt, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    {
+      int w = 0;
+      for (int t = 0; t < nt; ++t) {
+        if (std::sqrt(n1[t]) > 1e-8 * std::sqrt(n0[t]) && n1[t] > 0) {
+          if (w != t)
+            CK(cudaMemcpyAsync(Tt + (long)w * dim, Tt + (long)t * dim, sizeof(T) * dim,
+                               cudaMemcpyDeviceToDevice, c->st));
+          ++w;
+        }
+      }
+      nt = w;
+    }
+    if (nt == 0) break;
+    // CholQR2 among the new directions; a failing pivot drops that direction
+    for (int pass = 0; pass < 2; ++pass) {
+      while (true) {
+        CK((gemm<T, double>(false, true, nt, nt, (int)dim, 1.0, Tt, dim, Tt, dim, 0.0, Sg, nt, 0, c->st)));
+        CK(symmetrize(nt, Sg, nt, c->st));
+        CK(cholesky_inverse(nt, Sg, nt, Linv, info, c->st));
+        int hinfo = 0;
+        CK(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        if (hinfo == 0) break;
+        const int bad = hinfo - 1;
+        for (int t = bad + 1; t < nt; ++t)
+          CK(cudaMemcpyAsync(Tt + (long)(t - 1) * dim, Tt + (long)t * dim, sizeof(T) * dim,
+                             cudaMemcpyDeviceToDevice, c->st));
+        --nt;
+        if (nt == 0) break;
+      }
+      if (nt == 0) break;
+      CK((convert<double, T>((long)nt * nt, Linv, Lt, c->st)));
+      CK((gemm<T, T>(false, false, nt, (int)dim, nt, 1.0, Lt, nt, Tt, dim, 0.0, Tt2, dim, 1, c->st)));
+      std::swap(Tt, Tt2);
+    }
+    if (nt == 0) break;
+    CK(cudaMemcpyAsync(V + (long)m * dim, Tt, sizeof(T) * nt * dim, cudaMemcpyDeviceToDevice, c->st));
+    CA(timed_apply(nt, V + (long)m * dim, W + (long)m * dim));
+    m += nt;
+  }
+  for (int i = 0; i < ne; ++i) omega_out[i] = i < kk ? th[i] : NAN;
+  if (vec_out) CK(cudaMemcpyAsync(vec_out, X, sizeof(T) * (size_t)kk * dim, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (stats) {
+    stats->iterations = it;
+    stats->n_apply = n_apply;
+    stats->ms_apply = ms_apply;
+    stats->ms_total = std::chrono::duration<double, std::milli>(clk::now() - t_start).count();
+    double mx = 0;
+    for (int i = 0; i < kk; ++i) mx = std::max(mx, rn[i]);
+    stats->res_max = mx;
+    stats->precond_fallbacks = 0;
+  }
+  if (!converged) return fail(c, BSE_ERR_NOT_CONVERGED, "Davidson did not converge within max_it");
+  return BSE_OK;
+}
+
+}  // namespace
+
+// =================================================================================
+// C ABI
+// =================================================================================
+extern "C" {
+
+const char* bse_version(void) {
+  return "bse-gb300 0.1 (sm_103a; FP64 plain and FP32/FP64 mixed paths)";
+}
+
+const char* bse_last_error(const bse_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void bse_destroy(bse_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->st);
+  for (void* p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+  delete ctx;
+}
+
+int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) {
+  if (!out) return BSE_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!s) return BSE_ERR_INVALID_ARG;
+  if (precision != BSE_PREC_FP64 && precision != BSE_PREC_MIXED) return BSE_ERR_INVALID_ARG;
+  bse_ctx* c = new bse_ctx();
+  auto bail = [&](int code) { if (code != BSE_OK) { *out = c; } return code; };
+  c->st = (cudaStream_t)stream;
+  c->prec = precision;
+  if (!fft_supported(s->n_grid)) return bail(fail(c, BSE_ERR_INVALID_ARG, "n_grid must be one of 16, 32, 48, 64, 72, 96"));
+  if (!(s->L > 0) || s->n_half < 1 || s->n_occ < 1 || s->n_pdep < 0 || !s->miller || !s->psi ||
+      !s->eps || !s->v_loc || (s->n_pdep > 0 && (!s->pdep || !s->lambda)) || (s->spin != 0 && s->spin != 1))
+    return bail(fail(c, BSE_ERR_INVALID_ARG, "invalid system sizes or null pointers"));
+  if (s->overlap_thr <= 0 && s->keep_pairs < 1)
+    return bail(fail(c, BSE_ERR_INVALID_ARG, "need overlap_thr > 0 or keep_pairs >= 1"));
+  c->N = s->n_grid; c->n3 = (long)c->N * c->N * c->N; c->L = s->L; c->omega = s->L * s->L * s->L;
+  c->n_half = s->n_half; c->n_pw = 2 * s->n_half; c->n_occ = s->n_occ; c->n_pdep = s->n_pdep;
+  c->spin = s->spin; c->scissor = s->scissor; c->thr_in = s->overlap_thr; c->keep_pairs = s->keep_pairs;
+  if (c->n_occ >= c->n_pw - 1) return bail(fail(c, BSE_ERR_INVALID_ARG, "n_occ must be smaller than the sphere dimension"));
+  const int rmax = (c->N - 1) / 4;
+  std::vector<int> gpos(c->n_half), gneg(c->n_half);
+  for (int k = 0; k < c->n_half; ++k) {
+    const int* m = &s->miller[3 * k];
+    for (int a = 0; a < 3; ++a)
+      if (m[a] > rmax || m[a] < -rmax)
+        return bail(fail(c, BSE_ERR_INVALID_ARG, "miller index beyond (N-1)/4: products would alias"));
+    if (k == 0 && (m[0] | m[1] | m[2])) return bail(fail(c, BSE_ERR_INVALID_ARG, "miller[0] must be (0,0,0)"));
+    if (k > 0 && !(m[0] | m[1] | m[2])) return bail(fail(c, BSE_ERR_INVALID_ARG, "G = 0 appears twice"));
+    auto idx = [&](int x, int y, int z) {
+      x = (x % c->N + c->N) % c->N; y = (y % c->N + c->N) % c->N; z = (z % c->N + c->N) % c->N;
+      return x + c->N * (y + c->N * z);
+    };
+    gpos[k] = idx(m[0], m[1], m[2]);
+    gneg[k] = idx(-m[0], -m[1], -m[2]);
+  }
+  const long npsi = (long)c->n_occ * c->n_pw;
+  if (!all_finite(s->psi, npsi) || !all_finite(s->eps, c->n_occ) || !all_finite(s->v_loc, c->n3) ||
+      !std::isfinite(s->scissor) || (c->n_pdep > 0 && (!all_finite(s->pdep, (long)c->n_pdep * c->n_pw) ||
+                                                       !all_finite(s->lambda, c->n_pdep))))
+    return bail(fail(c, BSE_ERR_NUMERIC, "non-finite input"));
+  for (int v = 0; v < c->n_occ; ++v)
+    if (s->psi[(long)v * c->n_pw + 1] != 0.0) return bail(fail(c, BSE_ERR_INVALID_ARG, "psi pad entry (index 1) must be 0"));
+  for (int a = 0; a < c->n_pdep; ++a) {
+    if (s->pdep[(long)a * c->n_pw] != 0.0 || s->pdep[(long)a * c->n_pw + 1] != 0.0)
+      return bail(fail(c, BSE_ERR_INVALID_ARG, "pdep entries 0 and 1 must be 0"));
+    if (!(s->lambda[a] < 1.0)) return bail(fail(c, BSE_ERR_INVALID_ARG, "lambda must be < 1"));
+  }
+  // host tables
+  const double g = 2.0 * M_PI / c->L;
+  c->g2p_h.assign(c->n_pw, 0.0);
+  for (int k = 0; k < c->n_half; ++k) {
+    const int* m = &s->miller[3 * k];
+    const double g2 = g * g * (double)(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+    c->g2p_h[2 * k] = g2;
+    c->g2p_h[2 * k + 1] = (k == 0) ? 0.0 : g2;
+  }
+  c->eps_h.assign(s->eps, s->eps + c->n_occ);
+  double vs = 0;
+  for (long r = 0; r < c->n3; ++r) vs += s->v_loc[r];
+  c->v0 = vs / (double)c->n3;
+  std::vector<double> fh(std::max(1, c->n_pdep), 0.0);
+  for (int a = 0; a < c->n_pdep; ++a) fh[a] = s->lambda[a] / (1.0 - s->lambda[a]);
+  // workspace budget: BSE_WORKSPACE_GB or 40% of free memory, at most 64 GB
+  {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    size_t bud = std::min<size_t>((size_t)64 << 30, (size_t)(0.4 * (double)fr));
+    if (const char* e = getenv("BSE_WORKSPACE_GB")) bud = (size_t)(atof(e) * (double)(1ull << 30));
+    c->ws_budget = std::max<size_t>(bud, 1);
+  }
+  // device uploads
+#define UPLOAD(dst, src, n)                                                                    \
+  do {                                                                                         \
+    int _r = dalloc(c, &(dst), (size_t)(n));                                                   \
+    if (_r != BSE_OK) return bail(_r);                                                         \
+    cudaError_t _e = cudaMemcpyAsync(dst, src, sizeof(*(dst)) * (size_t)(n), cudaMemcpyHostToDevice, c->st); \
+    if (_e != cudaSuccess) return bail(cuda_fail(c, _e, "upload"));                            \
+  } while (0)
+  UPLOAD(c->gpos, gpos.data(), c->n_half);
+  UPLOAD(c->gneg, gneg.data(), c->n_half);
+  UPLOAD(c->g2p, c->g2p_h.data(), c->n_pw);
+  UPLOAD(c->eps, s->eps, c->n_occ);
+  UPLOAD(c->f, fh.data(), fh.size());
+  UPLOAD(c->psi64, s->psi, npsi);
+  UPLOAD(c->vloc64, s->v_loc, c->n3);
+  if (c->n_pdep > 0) UPLOAD(c->pdep64, s->pdep, (long)c->n_pdep * c->n_pw);
+  std::vector<double2> tw;
+  twiddle_table(c->N, tw);
+  UPLOAD(c->tw64, tw.data(), tw.size());
+  std::vector<float2> twf(tw.size());
+  for (size_t i = 0; i < tw.size(); ++i) { twf[i].x = (float)tw[i].x; twf[i].y = (float)tw[i].y; }
+  UPLOAD(c->tw32, twf.data(), twf.size());
+  // psi_v(r) (times Omega^{1/2}) in FP64 on the grid, pair layout
+  {
+    const long ng = (c->n_occ + 1) / 2;
+    double2* up;
+    int r = dalloc(c, &up, (size_t)ng * c->n3);
+    if (r != BSE_OK) return bail(r);
+    cudaError_t e = sphere_unpack<double, double>(c->psi64, c->n_occ, c->n_pw, c->n_half, c->gpos,
+                                                  c->gneg, up, c->n3, true, false, c->st);
+    if (e == cudaSuccess) e = fft3d<double>(up, ng, c->N, +1, c->tw64, c->st);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "psi to real space"));
+    c->upsi64 = (double*)up;
+    if (c->prec == BSE_PREC_MIXED) {
+      const long nr = ng * 2 * c->n3;
+      if ((r = dalloc(c, &c->upsi32, (size_t)nr)) != BSE_OK) return bail(r);
+      if ((r = dalloc(c, &c->psi32, (size_t)npsi)) != BSE_OK) return bail(r);
+      if ((r = dalloc(c, &c->vloc32, (size_t)c->n3)) != BSE_OK) return bail(r);
+      e = convert<double, float>(nr, c->upsi64, c->upsi32, c->st);
+      if (e == cudaSuccess) e = convert<double, float>(npsi, c->psi64, c->psi32, c->st);
+      if (e == cudaSuccess) e = convert<double, float>(c->n3, c->vloc64, c->vloc32, c->st);
+      if (e == cudaSuccess && c->n_pdep > 0) {
+        if ((r = dalloc(c, &c->pdep32, (size_t)c->n_pdep * c->n_pw)) != BSE_OK) return bail(r);
+        e = convert<double, float>((long)c->n_pdep * c->n_pw, c->pdep64, c->pdep32, c->st);
+      }
+      if (e != cudaSuccess) return bail(cuda_fail(c, e, "FP32 copies"));
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "bse_create"));
+  *out = c;
+  return BSE_OK;
+}
+
+int bse_build_tau(bse_ctx* c, int64_t* n_pairs_out, double* thr_out) {
+  if (!c) return BSE_ERR_INVALID_ARG;
+  int r = (c->prec == BSE_PREC_FP64) ? build_tau_impl<double>(c) : build_tau_impl<float>(c);
+  if (r != BSE_OK) return r;
+  if (n_pairs_out) *n_pairs_out = c->n_pairs;
+  if (thr_out) *thr_out = c->thr;
+  return BSE_OK;
+}
+
+int bse_get_pairs(const bse_ctx* c, int32_t* v_out, int32_t* w_out) {
+  if (!c || !v_out || !w_out) return BSE_ERR_INVALID_ARG;
+  if (!c->tau_ready) return BSE_ERR_STATE;
+  std::memcpy(v_out, c->pv_h.data(), sizeof(int32_t) * c->pv_h.size());
+  std::memcpy(w_out, c->pw_h.data(), sizeof(int32_t) * c->pw_h.size());
+  return BSE_OK;
+}
+
+int bse_get_overlaps(const bse_ctx* c, double* o_out) {
+  if (!c || !o_out) return BSE_ERR_INVALID_ARG;
+  if (c->O_h.empty()) return BSE_ERR_STATE;
+  std::memcpy(o_out, c->O_h.data(), sizeof(double) * c->O_h.size());
+  return BSE_OK;
+}
+
+int bse_apply_liouville(bse_ctx* c, int n_vec, const void* a_in, void* a_out) {
+  if (!c) return BSE_ERR_INVALID_ARG;
+  if (n_vec < 0 || (n_vec > 0 && (!a_in || !a_out))) return fail(c, BSE_ERR_INVALID_ARG, "bad apply arguments");
+  if (a_in == a_out && n_vec > 0) return fail(c, BSE_ERR_INVALID_ARG, "a_out must not alias a_in");
+  if (!c->tau_ready) return fail(c, BSE_ERR_STATE, "bse_build_tau must run before bse_apply_liouville");
+  int r = (c->prec == BSE_PREC_FP64)
+              ? apply_impl<double>(c, n_vec, (const double*)a_in, (double*)a_out)
+              : apply_impl<float>(c, n_vec, (const float*)a_in, (float*)a_out);
+  if (r != BSE_OK) return r;
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "bse_apply_liouville");
+  return BSE_OK;
+}
+
+int bse_davidson(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, void* vec_out,
+                 bse_davidson_stats* stats) {
+  if (!c) return BSE_ERR_INVALID_ARG;
+  if (!o || !omega_out) return fail(c, BSE_ERR_INVALID_ARG, "null options or omega_out");
+  if (!c->tau_ready) return fail(c, BSE_ERR_STATE, "bse_build_tau must run before bse_davidson");
+  return (c->prec == BSE_PREC_FP64)
+             ? davidson_impl<double>(c, o, omega_out, (double*)vec_out, stats)
+             : davidson_impl<float>(c, o, omega_out, (float*)vec_out, stats);
+}
+
+}  // extern "C"

@@ -1,0 +1,34 @@
+// Shared device helpers for the BSE hot-path kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+template <typename T> using cplx = typename cplx_of<T>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C cmk(double x, double y) {
+  C c; c.x = x; c.y = y; return c;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { a.x *= s; a.y *= s; return a; }
+// multiply by sign * i  (sign = +1 or -1)
+template <typename C> __device__ __forceinline__ C cmul_si(C a, int sign) {
+  C r; if (sign > 0) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; } return r;
+}
+
+// Real fields are stored two per complex grid ("pair layout"): field f lives in
+// component f%2 of complex grid f/2, i.e. at real offset (f/2)*2*n3 + 2*r + f%2.
+template <typename T>
+__device__ __forceinline__ size_t pair_off(long f, long r, long n3) {
+  return (size_t)(f >> 1) * 2 * (size_t)n3 + 2 * (size_t)r + (size_t)(f & 1);
+}
+
+__device__ __forceinline__ int iceil_div(int a, int b) { return (a + b - 1) / b; }

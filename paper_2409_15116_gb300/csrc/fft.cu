@@ -1,0 +1,362 @@
+// Batched 3D FFTs on N^3 grids (N in {16,32,48,64,72,96}) and plane-wave sphere
+// scatter / gather for Gamma-packed real fields.
+//
+// The transforms move the auxiliary orbitals a_sv, the pair densities of Eq. (k1e),
+// the densities psi_v psi_w of Eq. (tau) and the outputs of Eq. (evp) between the
+// plane-wave sphere and the real-space grid (the paper uses cuFFT, Section 3; these
+// kernels are written for sm_103a instead). Each 3D transform is three passes of
+// 1D transforms along x, y, z; a CTA moves TX lines of one axis into shared memory
+// (coalesced rows), runs a self-sorting (Stockham) mixed-radix transform with
+// radix-2/3/4/8 butterflies, and writes the lines back. Unnormalised:
+//   sign = -1:  F(n) = sum_m f(m) exp(-2 pi i n m / N)
+//   sign = +1:  f(m) = sum_n F(n) exp(+2 pi i n m / N)
+// Two real fields travel in one complex grid (real part = even field, imaginary
+// part = odd field); they separate again through Hermitian symmetry at the sphere.
+#include "common.cuh"
+#include "kernels.h"
+#include <cmath>
+#include <vector>
+
+namespace bse {
+
+// ---------------------------------------------------------------------------------
+// radix plans (product of radices = N)
+// ---------------------------------------------------------------------------------
+template <int N> struct Plan;
+template <> struct Plan<16> { static constexpr int n = 2, r0 = 4, r1 = 4, r2 = 1, TX = 16; };
+template <> struct Plan<32> { static constexpr int n = 2, r0 = 8, r1 = 4, r2 = 1, TX = 16; };
+template <> struct Plan<48> { static constexpr int n = 3, r0 = 4, r1 = 4, r2 = 3, TX = 16; };
+template <> struct Plan<64> { static constexpr int n = 2, r0 = 8, r1 = 8, r2 = 1, TX = 16; };
+template <> struct Plan<72> { static constexpr int n = 3, r0 = 8, r1 = 3, r2 = 3, TX = 24; };
+template <> struct Plan<96> { static constexpr int n = 3, r0 = 8, r1 = 4, r2 = 3, TX = 16; };
+
+// R-point DFT in registers, direction exp(sign * 2 pi i q r / R)
+template <typename C, int R> struct Dft;
+template <typename C> struct Dft<C, 2> {
+  static __device__ __forceinline__ void run(C* v, int) {
+    C a = v[0], b = v[1]; v[0] = cadd(a, b); v[1] = csub(a, b);
+  }
+};
+template <typename C> struct Dft<C, 3> {
+  static __device__ __forceinline__ void run(C* v, int sign) {
+    using T = decltype(v[0].x);
+    const T h = (T)0.86602540378443864676;   // sqrt(3)/2
+    C s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    C m; m.x = v[0].x - (T)0.5 * s.x; m.y = v[0].y - (T)0.5 * s.y;
+    C t = cmul_si(d, sign); t.x *= h; t.y *= h;
+    v[0] = cadd(v[0], s); v[1] = cadd(m, t); v[2] = csub(m, t);
+  }
+};
+template <typename C> struct Dft<C, 4> {
+  static __device__ __forceinline__ void run(C* v, int sign) {
+    C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+    C a2 = cadd(v[1], v[3]), a3 = cmul_si(csub(v[1], v[3]), sign);
+    v[0] = cadd(a0, a2); v[2] = csub(a0, a2); v[1] = cadd(a1, a3); v[3] = csub(a1, a3);
+  }
+};
+template <typename C> struct Dft<C, 8> {
+  static __device__ __forceinline__ void run(C* v, int sign) {
+    using T = decltype(v[0].x);
+    const T r2 = (T)0.70710678118654752440;   // 1/sqrt(2)
+    C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<C, 4>::run(e, sign); Dft<C, 4>::run(o, sign);
+    // twiddles w8^q = exp(sign 2 pi i q / 8)
+    C w1 = cmk<C>(r2, sign * r2), w3 = cmk<C>(-r2, sign * r2);
+    C t0 = o[0], t1 = cmul(o[1], w1), t2 = cmul_si(o[2], sign), t3 = cmul(o[3], w3);
+    v[0] = cadd(e[0], t0); v[4] = csub(e[0], t0);
+    v[1] = cadd(e[1], t1); v[5] = csub(e[1], t1);
+    v[2] = cadd(e[2], t2); v[6] = csub(e[2], t2);
+    v[3] = cadd(e[3], t3); v[7] = csub(e[3], t3);
+  }
+};
+
+// one Stockham stage of radix R over TX lines of length N (src -> dst, both smem)
+template <typename C, int N, int R, int TX>
+__device__ __forceinline__ void stage(const C* src, C* dst, const C* tw, int Ns, int sign) {
+  constexpr int NB = N / R;
+  const int step = N / (Ns * R);
+  for (int e = threadIdx.x; e < TX * NB; e += blockDim.x) {
+    const int i = e / NB, j = e - i * NB;
+    const int k = j % Ns;
+    const C* s = src + i * N;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = s[j + r * NB];
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[(r * k * step) % N]);
+    Dft<C, R>::run(v, sign);
+    C* d = dst + i * N + (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) d[r * Ns] = v[r];
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256) fft_axis_kernel(cplx<T>* __restrict__ data, int axis,
+                                                      int sign, const cplx<T>* __restrict__ table) {
+  using C = cplx<T>;
+  constexpr int TX = Plan<N>::TX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + TX * N;
+  C* tw = buf1 + TX * N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    C t = table[i];
+    if (sign > 0) t.y = -t.y;
+    tw[i] = t;
+  }
+  const long n3 = (long)N * N * N;
+  long base, sk, si;
+  if (axis == 0) {
+    base = (long)blockIdx.x * TX * N; sk = 1; si = N;
+  } else {
+    constexpr int nxt = N / TX;
+    long t = blockIdx.x;
+    const int xt = (int)(t % nxt); t /= nxt;
+    const int o = (int)(t % N);
+    const long b = t / N;
+    if (axis == 1) { base = b * n3 + (long)o * N * N + xt * TX; sk = N; }
+    else { base = b * n3 + (long)o * N + xt * TX; sk = (long)N * N; }
+    si = 1;
+  }
+  for (int e = threadIdx.x; e < TX * N; e += blockDim.x) {
+    int i, k;
+    if (axis == 0) { i = e / N; k = e - i * N; } else { k = e / TX; i = e - k * TX; }
+    buf0[i * N + k] = data[base + i * si + k * sk];
+  }
+  __syncthreads();
+  C* src = buf0; C* dst = buf1;
+  int Ns = 1;
+  stage<C, N, Plan<N>::r0, TX>(src, dst, tw, Ns, sign);
+  __syncthreads();
+  { C* t = src; src = dst; dst = t; } Ns *= Plan<N>::r0;
+  if constexpr (Plan<N>::n > 1) {
+    stage<C, N, Plan<N>::r1, TX>(src, dst, tw, Ns, sign);
+    __syncthreads();
+    { C* t = src; src = dst; dst = t; } Ns *= Plan<N>::r1;
+  }
+  if constexpr (Plan<N>::n > 2) {
+    stage<C, N, Plan<N>::r2, TX>(src, dst, tw, Ns, sign);
+    __syncthreads();
+    { C* t = src; src = dst; dst = t; }
+  }
+  for (int e = threadIdx.x; e < TX * N; e += blockDim.x) {
+    int i, k;
+    if (axis == 0) { i = e / N; k = e - i * N; } else { k = e / TX; i = e - k * TX; }
+    data[base + i * si + k * sk] = src[i * N + k];
+  }
+}
+
+template <typename T, int N>
+static cudaError_t launch_fft3d(cplx<T>* data, long n_batch, int sign, const cplx<T>* table,
+                                cudaStream_t st) {
+  constexpr int TX = Plan<N>::TX;
+  const size_t smem = (size_t)(2 * TX * N + N) * sizeof(cplx<T>);
+  static bool attr_set = false;   // per instantiation; attribute is per device function
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(fft_axis_kernel<T, N>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const long blocks = n_batch * (long)N * N / TX;
+  if (blocks <= 0) return cudaSuccess;
+  for (int axis = 0; axis < 3; ++axis) {
+    fft_axis_kernel<T, N><<<(unsigned)blocks, 256, smem, st>>>(data, axis, sign, table);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t fft3d(cplx<T>* data, long n_batch, int N, int sign, const cplx<T>* table,
+                  cudaStream_t st) {
+  switch (N) {
+    case 16: return launch_fft3d<T, 16>(data, n_batch, sign, table, st);
+    case 32: return launch_fft3d<T, 32>(data, n_batch, sign, table, st);
+    case 48: return launch_fft3d<T, 48>(data, n_batch, sign, table, st);
+    case 64: return launch_fft3d<T, 64>(data, n_batch, sign, table, st);
+    case 72: return launch_fft3d<T, 72>(data, n_batch, sign, table, st);
+    case 96: return launch_fft3d<T, 96>(data, n_batch, sign, table, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t fft3d<float>(float2*, long, int, int, const float2*, cudaStream_t);
+template cudaError_t fft3d<double>(double2*, long, int, int, const double2*, cudaStream_t);
+
+bool fft_supported(int N) {
+  return N == 16 || N == 32 || N == 48 || N == 64 || N == 72 || N == 96;
+}
+
+// exp(-2 pi i m / N), m = 0..N-1, computed on the host in double precision
+void twiddle_table(int N, std::vector<double2>& out) {
+  out.resize(N);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int m = 0; m < N; ++m) {
+    const double a = two_pi * (double)m / (double)N;
+    out[m].x = std::cos(a);
+    out[m].y = -std::sin(a);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// sphere scatter / gather
+// ---------------------------------------------------------------------------------
+
+// grids[c] (pre-zeroed) <- F = A + iB with A, B the packed fields 2c, 2c+1 (B = 0 if absent)
+template <typename T, typename TI>
+__global__ void sphere_unpack_kernel(const TI* __restrict__ P, long n_fields, int n_pw, int n_half,
+                                     const int* __restrict__ gpos, const int* __restrict__ gneg,
+                                     cplx<T>* __restrict__ grids, long n3, int accumulate) {
+  using C = cplx<T>;
+  const long n_c = (n_fields + 1) / 2;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_c * n_half) return;
+  const long c = idx / n_half;
+  const int k = (int)(idx - c * n_half);
+  const long fa = 2 * c, fb = 2 * c + 1;
+  const bool hb = fb < n_fields;
+  const T a0 = (T)P[fa * n_pw + 2 * k], a1 = (T)P[fa * n_pw + 2 * k + 1];
+  const T b0 = hb ? (T)P[fb * n_pw + 2 * k] : (T)0, b1 = hb ? (T)P[fb * n_pw + 2 * k + 1] : (T)0;
+  C* g = grids + c * n3;
+  if (k == 0) {
+    C F; F.x = a0; F.y = b0;
+    if (accumulate) F = cadd(g[gpos[0]], F);
+    g[gpos[0]] = F;
+    return;
+  }
+  const T s = (T)0.70710678118654752440;
+  // cA = (a0 + i a1)/sqrt2, cB = (b0 + i b1)/sqrt2
+  const T ax = a0 * s, ay = a1 * s, bx = b0 * s, by = b1 * s;
+  C Fp, Fm;
+  Fp.x = ax - by; Fp.y = ay + bx;       // cA + i cB
+  Fm.x = ax + by; Fm.y = -ay + bx;      // conj(cA) + i conj(cB)
+  if (accumulate) { Fp = cadd(g[gpos[k]], Fp); Fm = cadd(g[gneg[k]], Fm); }
+  g[gpos[k]] = Fp;
+  g[gneg[k]] = Fm;
+}
+
+// packed fields 2c, 2c+1 <- scale * grids[c] on the sphere (Hermitian separation), plus
+// the optional diagonal term (1/2|G|^2 + shift - eps[f % n_occ]) * add_in[f] (Eq. d).
+template <typename T, typename TO>
+__global__ void sphere_pack_kernel(const cplx<T>* __restrict__ grids, long n_fields, int n_pw,
+                                   int n_half, const int* __restrict__ gpos,
+                                   const int* __restrict__ gneg, long n3, double scale,
+                                   TO* __restrict__ out, const TO* __restrict__ add_in,
+                                   const double* __restrict__ g2p, const double* __restrict__ eps,
+                                   double shift, int n_occ) {
+  using C = cplx<T>;
+  const long n_c = (n_fields + 1) / 2;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_c * n_half) return;
+  const long c = idx / n_half;
+  const int k = (int)(idx - c * n_half);
+  const C* g = grids + c * n3;
+  const T sc = (T)scale;
+  C Fp = g[gpos[k]];
+  Fp.x *= sc; Fp.y *= sc;
+  T a0, a1, b0, b1;
+  if (k == 0) {
+    a0 = Fp.x; a1 = 0; b0 = Fp.y; b1 = 0;
+  } else {
+    C Fm = g[gneg[k]];
+    Fm.x *= sc; Fm.y *= sc;
+    const T r2 = (T)1.41421356237309504880;
+    // cA = (Fp + conj Fm)/2, cB = (Fp - conj Fm)/(2i)
+    a0 = (T)0.5 * (Fp.x + Fm.x) * r2;
+    a1 = (T)0.5 * (Fp.y - Fm.y) * r2;
+    b0 = (T)0.5 * (Fp.y + Fm.y) * r2;
+    b1 = (T)(-0.5) * (Fp.x - Fm.x) * r2;
+  }
+  const long fa = 2 * c, fb = 2 * c + 1;
+  const int j0 = 2 * k, j1 = 2 * k + 1;
+  if (add_in) {
+    const double ea = eps[fa % n_occ];
+    a0 += (T)((0.5 * g2p[j0] + shift - ea) * (double)add_in[fa * n_pw + j0]);
+    if (k) a1 += (T)((0.5 * g2p[j1] + shift - ea) * (double)add_in[fa * n_pw + j1]);
+  }
+  out[fa * n_pw + j0] = (TO)a0;
+  out[fa * n_pw + j1] = (TO)a1;
+  if (fb < n_fields) {
+    if (add_in) {
+      const double eb = eps[fb % n_occ];
+      b0 += (T)((0.5 * g2p[j0] + shift - eb) * (double)add_in[fb * n_pw + j0]);
+      if (k) b1 += (T)((0.5 * g2p[j1] + shift - eb) * (double)add_in[fb * n_pw + j1]);
+    }
+    out[fb * n_pw + j0] = (TO)b0;
+    out[fb * n_pw + j1] = (TO)b1;
+  }
+}
+
+template <typename T, typename TI>
+cudaError_t sphere_unpack(const TI* P, long n_fields, int n_pw, int n_half, const int* gpos,
+                          const int* gneg, cplx<T>* grids, long n3, bool zero_first,
+                          bool accumulate, cudaStream_t st) {
+  const long n_c = (n_fields + 1) / 2;
+  if (n_c == 0) return cudaSuccess;
+  if (zero_first) {
+    cudaError_t e = cudaMemsetAsync(grids, 0, (size_t)n_c * n3 * sizeof(cplx<T>), st);
+    if (e != cudaSuccess) return e;
+  }
+  const long total = n_c * n_half;
+  sphere_unpack_kernel<T, TI><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+      P, n_fields, n_pw, n_half, gpos, gneg, grids, n3, accumulate ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <typename T, typename TO>
+cudaError_t sphere_pack(const cplx<T>* grids, long n_fields, int n_pw, int n_half, const int* gpos,
+                        const int* gneg, long n3, double scale, TO* out, const TO* add_in,
+                        const double* g2p, const double* eps, double shift, int n_occ,
+                        cudaStream_t st) {
+  const long n_c = (n_fields + 1) / 2;
+  const long total = n_c * n_half;
+  if (total == 0) return cudaSuccess;
+  sphere_pack_kernel<T, TO><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+      grids, n_fields, n_pw, n_half, gpos, gneg, n3, scale, out, add_in, g2p, eps, shift, n_occ);
+  return cudaGetLastError();
+}
+
+template cudaError_t sphere_unpack<double, double>(const double*, long, int, int, const int*, const int*, double2*, long, bool, bool, cudaStream_t);
+template cudaError_t sphere_unpack<float, float>(const float*, long, int, int, const int*, const int*, float2*, long, bool, bool, cudaStream_t);
+template cudaError_t sphere_unpack<float, double>(const double*, long, int, int, const int*, const int*, float2*, long, bool, bool, cudaStream_t);
+template cudaError_t sphere_pack<double, double>(const double2*, long, int, int, const int*, const int*, long, double, double*, const double*, const double*, const double*, double, int, cudaStream_t);
+template cudaError_t sphere_pack<float, float>(const float2*, long, int, int, const int*, const int*, long, double, float*, const float*, const double*, const double*, double, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------------
+// multiply complex grids by a real, even function of |G| (keeps field pairs separable)
+//   mode 0: v(G)/Omega = 4 pi / (|G|^2 Omega), 0 at G = 0          (Hartree, Eq. k1e)
+//   mode 1: v(G)^{1/2} = sqrt(4 pi) / |G|, 0 at G = 0               (Eq. tau_from_tau_u)
+// ---------------------------------------------------------------------------------
+template <typename T>
+__global__ void grid_coulomb_kernel(cplx<T>* __restrict__ grids, long n_grids, int N, double L,
+                                    double omega, int mode, double scale) {
+  const long n3 = (long)N * N * N;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_grids * n3) return;
+  const long r = idx % n3;
+  const int x = (int)(r % N), y = (int)((r / N) % N), z = (int)(r / ((long)N * N));
+  const int nx = x < N / 2 ? x : x - N, ny = y < N / 2 ? y : y - N, nz = z < N / 2 ? z : z - N;
+  const double g = 6.283185307179586476925286766559 / L;
+  const double g2 = g * g * (double)(nx * nx + ny * ny + nz * nz);
+  double f = 0.0;
+  if (g2 > 0) f = (mode == 0) ? 12.566370614359172953850573533118 / (g2 * omega)
+                              : 3.5449077018110320545963349666823 / sqrt(g2);
+  f *= scale;
+  cplx<T> v = grids[idx];
+  v.x = (T)(v.x * f); v.y = (T)(v.y * f);
+  grids[idx] = v;
+}
+
+template <typename T>
+cudaError_t grid_coulomb(cplx<T>* grids, long n_grids, int N, double L, double omega, int mode,
+                         double scale, cudaStream_t st) {
+  const long total = n_grids * (long)N * N * N;
+  if (total == 0) return cudaSuccess;
+  grid_coulomb_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(grids, n_grids, N, L,
+                                                                         omega, mode, scale);
+  return cudaGetLastError();
+}
+template cudaError_t grid_coulomb<float>(float2*, long, int, double, double, int, double, cudaStream_t);
+template cudaError_t grid_coulomb<double>(double2*, long, int, double, double, int, double, cudaStream_t);
+
+}  // namespace bse

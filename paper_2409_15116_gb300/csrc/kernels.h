@@ -1,0 +1,76 @@
+// Internal launcher declarations (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <vector>
+#include "common.cuh"
+
+namespace bse {
+
+// ---- fft.cu ----
+bool fft_supported(int N);
+void twiddle_table(int N, std::vector<double2>& out);
+template <typename T>
+cudaError_t fft3d(cplx<T>* data, long n_batch, int N, int sign, const cplx<T>* table, cudaStream_t st);
+template <typename T, typename TI>
+cudaError_t sphere_unpack(const TI* P, long n_fields, int n_pw, int n_half, const int* gpos,
+                          const int* gneg, cplx<T>* grids, long n3, bool zero_first,
+                          bool accumulate, cudaStream_t st);
+template <typename T, typename TO>
+cudaError_t sphere_pack(const cplx<T>* grids, long n_fields, int n_pw, int n_half, const int* gpos,
+                        const int* gneg, long n3, double scale, TO* out, const TO* add_in,
+                        const double* g2p, const double* eps, double shift, int n_occ,
+                        cudaStream_t st);
+template <typename T>
+cudaError_t grid_coulomb(cplx<T>* grids, long n_grids, int N, double L, double omega, int mode,
+                         double scale, cudaStream_t st);
+
+// ---- gemm.cu ----
+template <typename T, typename TC>
+cudaError_t gemm(bool at, bool bt, int M, int N, int K, double alpha, const T* A, long lda,
+                 const T* B, long ldb, double beta, TC* C, long ldc, int splitk, cudaStream_t st);
+
+// ---- ops.cu ----
+template <typename T>
+cudaError_t pair_product(int nb, const int* pv, const int* pw, const T* upsi, long n3, double scale,
+                         cplx<T>* grids, cudaStream_t st);
+template <typename T>
+cudaError_t deinterleave_pairs(int nb, const cplx<T>* grids, long n3, T* tau, cudaStream_t st);
+cudaError_t square_fields(int n, const double* u, long n3, double* rho, cudaStream_t st);
+cudaError_t normalize_overlap(int n, double* gram, double* diag, cudaStream_t st);
+template <typename T>
+cudaError_t hartree_density(int n_vec, int n_occ, long n3, const T* a, const T* upsi, T* h,
+                            cudaStream_t st);
+template <typename T>
+cudaError_t k1d_combine(int n_vec, int n_occ, long n3, const T* a, const T* tau, const int* nbr_ptr,
+                        const int* nbr_w, const int* nbr_p, const T* vloc, const T* vh,
+                        const T* upsi, double spin_factor, T* out, cudaStream_t st);
+template <typename T>
+cudaError_t scale_columns(int rows, int cols, T* C, long ldc, const double* f, cudaStream_t st);
+template <typename TI, typename TO>
+cudaError_t convert(long n, const TI* in, TO* out, cudaStream_t st);
+template <typename T>
+cudaError_t pair_grid_to_rows(int n, const T* grids, long n3, T* rows, cudaStream_t st);
+template <typename T>
+cudaError_t residuals(int k, long dim, const T* X, const T* LX, const double* theta, T* R,
+                      double* norms2, cudaStream_t st);
+template <typename T>
+cudaError_t row_norms2(int k, long dim, const T* X, double* norms2, cudaStream_t st);
+template <typename T>
+cudaError_t precond_diag(int k, int n_occ, int n_pw, const T* R, const double* theta,
+                         const int* which, const double* g2p, const double* eps, double v0,
+                         double shift, T* out, cudaStream_t st);
+template <typename T>
+cudaError_t zero_pad_column(int rows, int n_pw, T* X, cudaStream_t st);
+template <typename T>
+cudaError_t scale_rows(int k, long dim, T* X, const double* s, cudaStream_t st);
+template <typename T>
+cudaError_t set_unit(T* x, long dim, long idx, cudaStream_t st);
+cudaError_t symmetrize(int m, double* A, long lda, cudaStream_t st);
+cudaError_t jacobi_eigh(int m, const double* A, long lda, double* work, double* V, double* w,
+                        int* info, cudaStream_t st);
+cudaError_t cholesky_inverse(int b, const double* S, long lds, double* Linv, int* info,
+                             cudaStream_t st);
+bool finite_check_host(const double* x, long n);
+
+}  // namespace bse

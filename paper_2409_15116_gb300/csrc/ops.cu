@@ -1,0 +1,604 @@
+// Pointwise, streaming and small dense kernels of the Liouville operator and the
+// Davidson solver.
+#include "common.cuh"
+#include "kernels.h"
+#include <cmath>
+
+namespace bse {
+
+static inline unsigned nblk(long total, int t = 256) { return (unsigned)((total + t - 1) / t); }
+
+// ---------------------------------------------------------------------------------
+// tau build: pair densities psi_v psi_w (Eq. tau), two pairs per complex grid
+// ---------------------------------------------------------------------------------
+template <typename T>
+__global__ void pair_product_kernel(int nb, const int* __restrict__ pv, const int* __restrict__ pw,
+                                    const T* __restrict__ upsi, long n3, T scale,
+                                    cplx<T>* __restrict__ grids) {
+  const long nc = (nb + 1) / 2;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nc * n3) return;
+  const long c = idx / n3, r = idx - c * n3;
+  const int p0 = (int)(2 * c), p1 = p0 + 1;
+  cplx<T> F;
+  F.x = upsi[pair_off<T>(pv[p0], r, n3)] * upsi[pair_off<T>(pw[p0], r, n3)] * scale;
+  F.y = p1 < nb ? upsi[pair_off<T>(pv[p1], r, n3)] * upsi[pair_off<T>(pw[p1], r, n3)] * scale : (T)0;
+  grids[idx] = F;
+}
+
+template <typename T>
+cudaError_t pair_product(int nb, const int* pv, const int* pw, const T* upsi, long n3, double scale,
+                         cplx<T>* grids, cudaStream_t st) {
+  const long tot = (long)((nb + 1) / 2) * n3;
+  if (!tot) return cudaSuccess;
+  pair_product_kernel<T><<<nblk(tot), 256, 0, st>>>(nb, pv, pw, upsi, n3, (T)scale, grids);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void deinterleave_kernel(int nb, const cplx<T>* __restrict__ grids, long n3,
+                                    T* __restrict__ tau) {
+  const long nc = (nb + 1) / 2;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nc * n3) return;
+  const long c = idx / n3, r = idx - c * n3;
+  const cplx<T> F = grids[idx];
+  tau[(2 * c) * n3 + r] = F.x;
+  if (2 * c + 1 < nb) tau[(2 * c + 1) * n3 + r] = F.y;
+}
+
+template <typename T>
+cudaError_t deinterleave_pairs(int nb, const cplx<T>* grids, long n3, T* tau, cudaStream_t st) {
+  const long tot = (long)((nb + 1) / 2) * n3;
+  if (!tot) return cudaSuccess;
+  deinterleave_kernel<T><<<nblk(tot), 256, 0, st>>>(nb, grids, n3, tau);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// overlap (Eq. overlap): |psi_v|^2 on the grid, Gram by GEMM, then normalisation
+// ---------------------------------------------------------------------------------
+__global__ void square_fields_kernel(int n, const double* __restrict__ u, long n3,
+                                     double* __restrict__ rho) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)n * n3) return;
+  const long v = idx / n3, r = idx - v * n3;
+  const double x = u[pair_off<double>(v, r, n3)];
+  rho[idx] = x * x;
+}
+cudaError_t square_fields(int n, const double* u, long n3, double* rho, cudaStream_t st) {
+  const long tot = (long)n * n3;
+  if (!tot) return cudaSuccess;
+  square_fields_kernel<<<nblk(tot), 256, 0, st>>>(n, u, n3, rho);
+  return cudaGetLastError();
+}
+
+__global__ void overlap_diag_kernel(int n, const double* g, double* d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = g[(long)i * n + i];
+}
+__global__ void normalize_overlap_kernel(int n, double* g, const double* d) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx - (long)i * n);
+  g[idx] = (i == j) ? 1.0 : g[idx] / sqrt(d[i] * d[j]);
+}
+// O_vw = Gram_vw / sqrt(Gram_vv Gram_ww); the diagonal becomes exactly 1
+cudaError_t normalize_overlap(int n, double* gram, double* diag, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  overlap_diag_kernel<<<nblk(n), 256, 0, st>>>(n, gram, diag);
+  normalize_overlap_kernel<<<nblk((long)n * n), 256, 0, st>>>(n, gram, diag);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// Hartree pair density of Eq. (k1e): h_s(r) = sum_w u_psi_w(r) u_a_sw(r)
+// ---------------------------------------------------------------------------------
+template <typename T>
+__global__ void hartree_density_kernel(int n_vec, int n_occ, long n3, const T* __restrict__ a,
+                                       const T* __restrict__ upsi, T* __restrict__ h) {
+  const long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (r >= n3) return;
+  T acc = 0;
+  const long f0 = (long)s * n_occ;
+  for (int w = 0; w < n_occ; ++w) acc += upsi[pair_off<T>(w, r, n3)] * a[pair_off<T>(f0 + w, r, n3)];
+  h[pair_off<T>(s, r, n3)] = acc;
+}
+template <typename T>
+cudaError_t hartree_density(int n_vec, int n_occ, long n3, const T* a, const T* upsi, T* h,
+                            cudaStream_t st) {
+  if (!n_vec) return cudaSuccess;
+  dim3 grid(nblk(n3), n_vec);
+  hartree_density_kernel<T><<<grid, 256, 0, st>>>(n_vec, n_occ, n3, a, upsi, h);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// screened direct term (Eq. k1d) fused with the real-space part of D (Eq. d) and
+// K1e (Eq. k1e):
+//   u_R,sv(r) = V_loc(r) u_a,sv(r) + s V_H,s(r) u_psi,v(r) - sum_{w in nbr(v)} tau_vw(r) u_a,sw(r)
+// ---------------------------------------------------------------------------------
+template <typename T, int SCH>
+__global__ void __launch_bounds__(256) k1d_combine_kernel(
+    int n_vec, int n_occ, long n3, const T* __restrict__ a, const T* __restrict__ tau,
+    const int* __restrict__ nbr_ptr, const int* __restrict__ nbr_w, const int* __restrict__ nbr_p,
+    const T* __restrict__ vloc, const T* __restrict__ vh, const T* __restrict__ upsi, T sf,
+    T* __restrict__ out) {
+  const long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n3) return;
+  const int v = blockIdx.y;
+  const int s0 = blockIdx.z * SCH;
+  T acc[SCH];
+#pragma unroll
+  for (int j = 0; j < SCH; ++j) acc[j] = 0;
+  const int e0 = nbr_ptr[v], e1 = nbr_ptr[v + 1];
+  for (int e = e0; e < e1; ++e) {
+    const int w = nbr_w[e];
+    const T t = tau[(long)nbr_p[e] * n3 + r];
+#pragma unroll
+    for (int j = 0; j < SCH; ++j) {
+      const int s = s0 + j;
+      if (s < n_vec) acc[j] += t * a[pair_off<T>((long)s * n_occ + w, r, n3)];
+    }
+  }
+  const T vl = vloc[r];
+  const T up = upsi[pair_off<T>(v, r, n3)];
+#pragma unroll
+  for (int j = 0; j < SCH; ++j) {
+    const int s = s0 + j;
+    if (s >= n_vec) break;
+    const long f = (long)s * n_occ + v;
+    out[pair_off<T>(f, r, n3)] = vl * a[pair_off<T>(f, r, n3)] + sf * vh[pair_off<T>(s, r, n3)] * up - acc[j];
+  }
+}
+
+template <typename T>
+cudaError_t k1d_combine(int n_vec, int n_occ, long n3, const T* a, const T* tau, const int* nbr_ptr,
+                        const int* nbr_w, const int* nbr_p, const T* vloc, const T* vh,
+                        const T* upsi, double spin_factor, T* out, cudaStream_t st) {
+  constexpr int SCH = 8;
+  if (!n_vec) return cudaSuccess;
+  dim3 grid(nblk(n3), n_occ, (n_vec + SCH - 1) / SCH);
+  k1d_combine_kernel<T, SCH><<<grid, 256, 0, st>>>(n_vec, n_occ, n3, a, tau, nbr_ptr, nbr_w, nbr_p,
+                                                   vloc, vh, upsi, (T)spin_factor, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------------
+template <typename T>
+__global__ void scale_columns_kernel(int rows, int cols, T* C, long ldc, const double* f) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)rows * cols) return;
+  const long i = idx / cols, j = idx - i * cols;
+  C[i * ldc + j] = (T)((double)C[i * ldc + j] * f[j]);
+}
+template <typename T>
+cudaError_t scale_columns(int rows, int cols, T* C, long ldc, const double* f, cudaStream_t st) {
+  const long tot = (long)rows * cols;
+  if (!tot) return cudaSuccess;
+  scale_columns_kernel<T><<<nblk(tot), 256, 0, st>>>(rows, cols, C, ldc, f);
+  return cudaGetLastError();
+}
+
+template <typename TI, typename TO>
+__global__ void convert_kernel(long n, const TI* in, TO* out) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (TO)in[i];
+}
+template <typename TI, typename TO>
+cudaError_t convert(long n, const TI* in, TO* out, cudaStream_t st) {
+  if (!n) return cudaSuccess;
+  convert_kernel<TI, TO><<<nblk(n), 256, 0, st>>>(n, in, out);
+  return cudaGetLastError();
+}
+
+// real fields of a pair-layout buffer -> rows [n][n3]
+template <typename T>
+__global__ void pair_grid_to_rows_kernel(int n, const T* g, long n3, T* rows) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)n * n3) return;
+  const long f = idx / n3, r = idx - f * n3;
+  rows[idx] = g[pair_off<T>(f, r, n3)];
+}
+template <typename T>
+cudaError_t pair_grid_to_rows(int n, const T* grids, long n3, T* rows, cudaStream_t st) {
+  const long tot = (long)n * n3;
+  if (!tot) return cudaSuccess;
+  pair_grid_to_rows_kernel<T><<<nblk(tot), 256, 0, st>>>(n, grids, n3, rows);
+  return cudaGetLastError();
+}
+
+// block reduction of doubles
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  __syncthreads();   // previous users of sh are done
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[lane] : 0.0;
+  if (wid == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// R_i = LX_i - theta_i X_i and ||R_i||^2 (FP64 accumulation)
+template <typename T>
+__global__ void residual_kernel(long dim, const T* X, const T* LX, const double* theta, T* R,
+                                double* norms2) {
+  __shared__ double sh[32];
+  const int i = blockIdx.y;
+  const double th = theta[i];
+  double acc = 0;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < dim; e += (long)gridDim.x * blockDim.x) {
+    const double r = (double)LX[i * dim + e] - th * (double)X[i * dim + e];
+    R[i * dim + e] = (T)r;
+    acc += r * r;
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) atomicAdd(norms2 + i, acc);
+}
+template <typename T>
+cudaError_t residuals(int k, long dim, const T* X, const T* LX, const double* theta, T* R,
+                      double* norms2, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(norms2, 0, sizeof(double) * k, st);
+  if (e != cudaSuccess) return e;
+  long nb = (dim + 255) / 256;
+  if (nb > 592) nb = 592;
+  dim3 grid((unsigned)nb, k);
+  residual_kernel<T><<<grid, 256, 0, st>>>(dim, X, LX, theta, R, norms2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void row_norms2_kernel(long dim, const T* X, double* norms2) {
+  __shared__ double sh[32];
+  const int i = blockIdx.y;
+  double acc = 0;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < dim; e += (long)gridDim.x * blockDim.x) {
+    const double x = (double)X[i * dim + e];
+    acc += x * x;
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) atomicAdd(norms2 + i, acc);
+}
+template <typename T>
+cudaError_t row_norms2(int k, long dim, const T* X, double* norms2, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(norms2, 0, sizeof(double) * k, st);
+  if (e != cudaSuccess || !k) return e;
+  long nb = (dim + 255) / 256;
+  if (nb > 592) nb = 592;
+  dim3 grid((unsigned)nb, k);
+  row_norms2_kernel<T><<<grid, 256, 0, st>>>(dim, X, norms2);
+  return cudaGetLastError();
+}
+
+// diagonal preconditioner t = r / (d - theta), d = 1/2|G|^2 + V(0) + Delta - eps_v,
+// |d - theta| clamped to >= 1e-2 with its sign; the pad coordinate is set to 0
+template <typename T>
+__global__ void precond_diag_kernel(int n_occ, int n_pw, const T* R, const double* theta,
+                                    const int* which, const double* g2p, const double* eps,
+                                    double v0, double shift, T* out) {
+  const long dim = (long)n_occ * n_pw;
+  const int t = blockIdx.y;
+  const int i = which[t];
+  const double th = theta[i];
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < dim; e += (long)gridDim.x * blockDim.x) {
+    const int v = (int)(e / n_pw), j = (int)(e - (long)v * n_pw);
+    double den = 0.5 * g2p[j] + v0 + shift - eps[v] - th;
+    if (fabs(den) < 1e-2) den = den >= 0 ? 1e-2 : -1e-2;
+    out[t * dim + e] = (j == 1) ? (T)0 : (T)((double)R[(long)i * dim + e] / den);
+  }
+}
+template <typename T>
+cudaError_t precond_diag(int k, int n_occ, int n_pw, const T* R, const double* theta,
+                         const int* which, const double* g2p, const double* eps, double v0,
+                         double shift, T* out, cudaStream_t st) {
+  if (!k) return cudaSuccess;
+  const long dim = (long)n_occ * n_pw;
+  long nb = (dim + 255) / 256;
+  if (nb > 1184) nb = 1184;
+  dim3 grid((unsigned)nb, k);
+  precond_diag_kernel<T><<<grid, 256, 0, st>>>(n_occ, n_pw, R, theta, which, g2p, eps, v0, shift, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void zero_pad_kernel(int rows, int n_pw, T* X) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < rows) X[i * n_pw + 1] = (T)0;
+}
+template <typename T>
+cudaError_t zero_pad_column(int rows, int n_pw, T* X, cudaStream_t st) {
+  if (!rows) return cudaSuccess;
+  zero_pad_kernel<T><<<nblk(rows), 256, 0, st>>>(rows, n_pw, X);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void scale_rows_kernel(long dim, T* X, const double* s) {
+  const int i = blockIdx.y;
+  const double f = s[i];
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < dim; e += (long)gridDim.x * blockDim.x)
+    X[i * dim + e] = (T)((double)X[i * dim + e] * f);
+}
+template <typename T>
+cudaError_t scale_rows(int k, long dim, T* X, const double* s, cudaStream_t st) {
+  if (!k) return cudaSuccess;
+  long nb = (dim + 255) / 256;
+  if (nb > 1184) nb = 1184;
+  dim3 grid((unsigned)nb, k);
+  scale_rows_kernel<T><<<grid, 256, 0, st>>>(dim, X, s);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void set_unit_kernel(T* x, long idx) { x[idx] = (T)1; }
+template <typename T>
+cudaError_t set_unit(T* x, long dim, long idx, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(x, 0, sizeof(T) * dim, st);
+  if (e != cudaSuccess) return e;
+  set_unit_kernel<T><<<1, 1, 0, st>>>(x, idx);
+  return cudaGetLastError();
+}
+
+__global__ void symmetrize_kernel(int m, double* A, long lda) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)m * m) return;
+  const int i = (int)(idx / m), j = (int)(idx - (long)i * m);
+  if (j <= i) return;
+  const double v = 0.5 * (A[(long)i * lda + j] + A[(long)j * lda + i]);
+  A[(long)i * lda + j] = v;
+  A[(long)j * lda + i] = v;
+}
+cudaError_t symmetrize(int m, double* A, long lda, cudaStream_t st) {
+  const long tot = (long)m * m;
+  if (!tot) return cudaSuccess;
+  symmetrize_kernel<<<nblk(tot), 256, 0, st>>>(m, A, lda);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// FP64 symmetric eigensolver for the Rayleigh-Ritz matrix: cyclic two-sided Jacobi
+// with round-robin parallel ordering (disjoint rotations applied together), one CTA.
+// A (m x m, symmetric) is read; eigenvalues ascending in w, eigenvectors as the
+// columns of V (m x m, row-major). work: m*m doubles. info: sweeps used (or -1).
+// ---------------------------------------------------------------------------------
+constexpr int JACOBI_MAX = 160;
+
+__global__ void __launch_bounds__(512) jacobi_kernel(int m, const double* __restrict__ Ain, long lda,
+                                                    double* __restrict__ Vw, double* __restrict__ V,
+                                                    double* __restrict__ w, int* info) {
+  extern __shared__ __align__(16) double jsm[];
+  const int ld = m + 1;
+  double* A = jsm;                              // m x (m+1)
+  double* cs = A + (long)m * ld;                // c[m/2+1], s[m/2+1]
+  double* sn = cs + (m / 2 + 1);
+  int* pp = reinterpret_cast<int*>(sn + (m / 2 + 1));
+  int* qq = pp + (m / 2 + 1);
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (long e = tid; e < (long)m * m; e += nt) {
+    const int i = (int)(e / m), j = (int)(e - (long)i * m);
+    A[i * ld + j] = Ain[(long)i * lda + j];
+    Vw[e] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int mp = (m + 1) & ~1;     // even number of players (index m is a bye when m is odd)
+  const int half = mp / 2;
+  // Frobenius norm for the stopping test
+  double fro = 0;
+  for (long e = tid; e < (long)m * m; e += nt) {
+    const int i = (int)(e / m), j = (int)(e - (long)i * m);
+    fro += A[i * ld + j] * A[i * ld + j];
+  }
+  fro = block_sum(fro, red);
+  __shared__ double fro_s;
+  if (tid == 0) fro_s = fro;
+  __syncthreads();
+  const double tol2 = 1e-26 * fro_s;   // stop when ||offdiag||_F <= 1e-13 ||A||_F
+  __shared__ double off_s;
+  int sweep = 0;
+  for (; sweep < 30; ++sweep) {
+    double off = 0;
+    for (long e = tid; e < (long)m * m; e += nt) {
+      const int i = (int)(e / m), j = (int)(e - (long)i * m);
+      if (i != j) off += A[i * ld + j] * A[i * ld + j];
+    }
+    __syncthreads();
+    off = block_sum(off, red);
+    if (tid == 0) off_s = off;
+    __syncthreads();
+    if (off_s <= tol2 || m < 2) break;
+    for (int rnd = 0; rnd < mp - 1; ++rnd) {
+      for (int t = tid; t < half; t += nt) {
+        int p = (t == 0) ? 0 : ((t - 1 + rnd) % (mp - 1)) + 1;
+        const int u = mp - 1 - t;
+        int q = ((u - 1 + rnd) % (mp - 1)) + 1;
+        if (p > q) { const int x = p; p = q; q = x; }
+        double c = 1.0, s = 0.0;
+        if (q < m) {
+          const double apq = A[p * ld + q];
+          if (apq != 0.0) {
+            const double tau = (A[q * ld + q] - A[p * ld + p]) / (2.0 * apq);
+            const double tt = (tau >= 0) ? 1.0 / (tau + sqrt(1.0 + tau * tau))
+                                         : -1.0 / (-tau + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + tt * tt);
+            s = tt * c;
+          }
+        }
+        pp[t] = p; qq[t] = q; cs[t] = c; sn[t] = s;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (long e = tid; e < (long)half * m; e += nt) {
+        const int t = (int)(e / m), k = (int)(e - (long)t * m);
+        const int p = pp[t], q = qq[t];
+        if (q >= m || sn[t] == 0.0) continue;
+        const double c = cs[t], s = sn[t];
+        const double ap = A[p * ld + k], aq = A[q * ld + k];
+        A[p * ld + k] = c * ap - s * aq;
+        A[q * ld + k] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (long e = tid; e < (long)half * m; e += nt) {
+        const int t = (int)(e / m), k = (int)(e - (long)t * m);
+        const int p = pp[t], q = qq[t];
+        if (q >= m || sn[t] == 0.0) continue;
+        const double c = cs[t], s = sn[t];
+        const double ap = A[k * ld + p], aq = A[k * ld + q];
+        A[k * ld + p] = c * ap - s * aq;
+        A[k * ld + q] = s * ap + c * aq;
+        const double vp = Vw[(long)k * m + p], vq = Vw[(long)k * m + q];
+        Vw[(long)k * m + p] = c * vp - s * vq;
+        Vw[(long)k * m + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  // sort ascending (stable by index) and permute the eigenvector columns
+  for (int i = tid; i < m; i += nt) {
+    const double di = A[i * ld + i];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      const double dj = A[j * ld + j];
+      rank += (dj < di) || (dj == di && j < i);
+    }
+    w[rank] = di;
+  }
+  __syncthreads();
+  for (long e = tid; e < (long)m * m; e += nt) {
+    const int k = (int)(e / m), i = (int)(e - (long)k * m);
+    const double di = A[i * ld + i];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      const double dj = A[j * ld + j];
+      rank += (dj < di) || (dj == di && j < i);
+    }
+    V[(long)k * m + rank] = Vw[e];
+  }
+  if (tid == 0) info[0] = (sweep >= 30) ? -1 : sweep;
+}
+
+cudaError_t jacobi_eigh(int m, const double* A, long lda, double* work, double* V, double* w,
+                        int* info, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  if (m > JACOBI_MAX) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)m * (m + 1) * sizeof(double) + 2 * (m / 2 + 1) * sizeof(double) +
+                      2 * (m / 2 + 1) * sizeof(int) + 64;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((size_t)JACOBI_MAX * (JACOBI_MAX + 1) * 8 + 4096));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  jacobi_kernel<<<1, 512, smem, st>>>(m, A, lda, work, V, w, info);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// Cholesky S = L L^T (b x b, FP64) and Linv = L^{-1} (lower), one CTA.
+// info[0] = 0 on success, j+1 if the j-th pivot is not positive and finite.
+// ---------------------------------------------------------------------------------
+constexpr int CHOL_MAX = 128;
+__global__ void __launch_bounds__(256) cholesky_kernel(int b, const double* __restrict__ S, long lds,
+                                                      double* __restrict__ Linv, int* info) {
+  extern __shared__ __align__(16) double csm[];
+  const int ld = b + 1;
+  double* A = csm;
+  __shared__ int bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (long e = tid; e < (long)b * b; e += nt) {
+    const int i = (int)(e / b), j = (int)(e - (long)i * b);
+    A[i * ld + j] = S[(long)i * lds + j];
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {
+    if (tid == 0) {
+      const double d = A[j * ld + j];
+      if (!(d > 0.0) || !isfinite(d)) { if (!bad) bad = j + 1; A[j * ld + j] = 1.0; }
+      else A[j * ld + j] = sqrt(d);
+    }
+    __syncthreads();
+    const double djj = A[j * ld + j];
+    for (int i = j + 1 + tid; i < b; i += nt) A[i * ld + j] /= djj;
+    __syncthreads();
+    for (long e = tid; e < (long)(b - j - 1) * (b - j - 1); e += nt) {
+      const int i = j + 1 + (int)(e / (b - j - 1)), k = j + 1 + (int)(e % (b - j - 1));
+      if (k <= i) A[i * ld + k] -= A[i * ld + j] * A[k * ld + j];
+    }
+    __syncthreads();
+  }
+  // Linv column c by forward substitution
+  for (int c = tid; c < b; c += nt) {
+    for (int i = 0; i < b; ++i) {
+      double x;
+      if (i < c) x = 0.0;
+      else {
+        double sacc = (i == c) ? 1.0 : 0.0;
+        for (int k = c; k < i; ++k) sacc -= A[i * ld + k] * Linv[(long)k * b + c];
+        x = sacc / A[i * ld + i];
+      }
+      Linv[(long)i * b + c] = x;
+    }
+  }
+  if (tid == 0) info[0] = bad;
+}
+
+cudaError_t cholesky_inverse(int b, const double* S, long lds, double* Linv, int* info,
+                             cudaStream_t st) {
+  if (b <= 0) return cudaSuccess;
+  if (b > CHOL_MAX) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)b * (b + 1) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((size_t)CHOL_MAX * (CHOL_MAX + 1) * 8));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  cholesky_kernel<<<1, 256, smem, st>>>(b, S, lds, Linv, info);
+  return cudaGetLastError();
+}
+
+bool finite_check_host(const double* x, long n) {
+  for (long i = 0; i < n; ++i)
+    if (!std::isfinite(x[i])) return false;
+  return true;
+}
+
+// ---------------------------------------------------------------------------------
+// explicit instantiations
+// ---------------------------------------------------------------------------------
+#define INST_T(T)                                                                                  \
+  template cudaError_t pair_product<T>(int, const int*, const int*, const T*, long, double,        \
+                                       cplx<T>*, cudaStream_t);                                    \
+  template cudaError_t deinterleave_pairs<T>(int, const cplx<T>*, long, T*, cudaStream_t);         \
+  template cudaError_t hartree_density<T>(int, int, long, const T*, const T*, T*, cudaStream_t);   \
+  template cudaError_t k1d_combine<T>(int, int, long, const T*, const T*, const int*, const int*,   \
+                                      const int*, const T*, const T*, const T*, double, T*,        \
+                                      cudaStream_t);                                               \
+  template cudaError_t scale_columns<T>(int, int, T*, long, const double*, cudaStream_t);          \
+  template cudaError_t pair_grid_to_rows<T>(int, const T*, long, T*, cudaStream_t);                \
+  template cudaError_t residuals<T>(int, long, const T*, const T*, const double*, T*, double*,     \
+                                    cudaStream_t);                                                 \
+  template cudaError_t row_norms2<T>(int, long, const T*, double*, cudaStream_t);                  \
+  template cudaError_t precond_diag<T>(int, int, int, const T*, const double*, const int*,         \
+                                       const double*, const double*, double, double, T*,           \
+                                       cudaStream_t);                                              \
+  template cudaError_t zero_pad_column<T>(int, int, T*, cudaStream_t);                             \
+  template cudaError_t scale_rows<T>(int, long, T*, const double*, cudaStream_t);                  \
+  template cudaError_t set_unit<T>(T*, long, long, cudaStream_t);
+INST_T(float)
+INST_T(double)
+template cudaError_t convert<double, float>(long, const double*, float*, cudaStream_t);
+template cudaError_t convert<float, double>(long, const float*, double*, cudaStream_t);
+template cudaError_t convert<double, double>(long, const double*, double*, cudaStream_t);
+template cudaError_t convert<float, float>(long, const float*, float*, cudaStream_t);
+
+}  // namespace bse
