@@ -112,7 +112,8 @@ typedef struct {
   int max_sub;      /* maximum subspace size; restart keeps 2*n_eig Ritz vectors */
   int max_it;       /* iteration limit */
   double res_tol;   /* converged when every ||L x - theta x||_2 <= res_tol (Ha) */
-  int precond;      /* 0 diagonal, 1 learned (falls back to diagonal if no net loaded) */
+  int precond;      /* 0 diagonal: t = P_c r / max(1/2|G|^2 + V(0) + Delta - eps_v - theta, 0.1 Ha);
+                       1 learned (falls back to diagonal if no net loaded) */
 } bse_davidson_opts;
 
 typedef struct {
@@ -130,6 +131,27 @@ typedef struct {
  * On BSE_ERR_NOT_CONVERGED omega_out, vec_out and stats hold the last Ritz pairs. */
 int bse_davidson(bse_ctx* ctx, const bse_davidson_opts* opts, double* omega_out,
                  void* vec_out, bse_davidson_stats* stats);
+
+/* Per-region profile (library addition; the paper reports module wall times only,
+ * Fig. 3). When enabled, each instrumented region of the hot path is bracketed by
+ * CUDA events recorded on the context stream, so a region's time is the device time
+ * of the kernels it launches. bytes / flops are the region's ALGORITHMIC traffic and
+ * work (each operand read once, each result written once), not measured counters. */
+typedef struct {
+  char name[32];
+  int64_t calls;   /* times the region ran */
+  double ms;       /* summed device time */
+  double bytes;    /* summed algorithmic bytes */
+  double flops;    /* summed algorithmic floating-point operations */
+} bse_prof_entry;
+
+/* mode 1: enable, 0: disable, -1: clear accumulated entries. */
+int bse_profile(bse_ctx* ctx, int mode);
+
+/* Copies up to cap entries to out (nullable), sets *n_out (nullable) to the number of
+ * regions and *launches (nullable) to the kernel launches this library has issued in
+ * this process. ctx may be NULL to read the launch count alone. */
+int bse_profile_read(bse_ctx* ctx, bse_prof_entry* out, int cap, int* n_out, int64_t* launches);
 
 /* Human-readable description of the last error on this context (never NULL). */
 const char* bse_last_error(const bse_ctx* ctx);

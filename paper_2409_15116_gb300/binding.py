@@ -25,7 +25,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 # every symbol include/bse.h declares
 EXPORTS = ["bse_create", "bse_build_tau", "bse_get_pairs", "bse_get_overlaps",
            "bse_apply_liouville", "bse_davidson", "bse_last_error", "bse_version",
-           "bse_destroy"]
+           "bse_destroy", "bse_profile", "bse_profile_read"]
 
 
 class BseError(RuntimeError):
@@ -42,6 +42,11 @@ class System(C.Structure):
                 ("n_pdep", C.c_int), ("pdep", C.POINTER(C.c_double)),
                 ("lam", C.POINTER(C.c_double)), ("overlap_thr", C.c_double),
                 ("keep_pairs", C.c_int64), ("spin", C.c_int)]
+
+
+class ProfEntry(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("calls", C.c_int64), ("ms", C.c_double),
+                ("bytes", C.c_double), ("flops", C.c_double)]
 
 
 class DavidsonOpts(C.Structure):
@@ -77,6 +82,9 @@ def load(path: str = LIB_PATH):
     lib.bse_last_error.argtypes = [P]
     lib.bse_last_error.restype = C.c_char_p
     lib.bse_version.restype = C.c_char_p
+    lib.bse_profile.argtypes = [P, C.c_int]
+    lib.bse_profile_read.argtypes = [P, C.POINTER(ProfEntry), C.c_int, C.POINTER(C.c_int),
+                                     C.POINTER(C.c_int64)]
     lib.bse_destroy.argtypes = [P]
     lib.bse_destroy.restype = None
     for name in EXPORTS:
@@ -147,6 +155,23 @@ class Context:
         except Exception:
             pass
 
+    def profile(self, mode: int):
+        """1 enable, 0 disable, -1 clear the per-region CUDA-event profile."""
+        self._check(self.lib.bse_profile(self.h, int(mode)))
+
+    def profile_read(self):
+        """({region: dict(calls, ms, bytes, flops)}, kernel launches issued so far)."""
+        n = C.c_int()
+        nl = C.c_int64()
+        self._check(self.lib.bse_profile_read(self.h, None, 0, C.byref(n), C.byref(nl)))
+        buf = (ProfEntry * max(1, n.value))()
+        self._check(self.lib.bse_profile_read(self.h, buf, n.value, C.byref(n), C.byref(nl)))
+        out = {}
+        for e in buf[:n.value]:
+            out[e.name.decode()] = dict(calls=int(e.calls), ms=float(e.ms), bytes=float(e.bytes),
+                                        flops=float(e.flops))
+        return out, int(nl.value)
+
     def build_tau(self):
         n = C.c_int64()
         t = C.c_double()
@@ -192,3 +217,10 @@ class Context:
 
 def version() -> str:
     return load().bse_version().decode()
+
+
+def launch_count() -> int:
+    """Kernel launches issued by the library in this process."""
+    nl = C.c_int64()
+    load().bse_profile_read(None, None, 0, None, C.byref(nl))
+    return int(nl.value)

@@ -15,7 +15,48 @@
 
 using namespace bse;
 
+// ---------------------------------------------------------------------------------
+// region profiler: CUDA events on the context stream around instrumented regions
+// ---------------------------------------------------------------------------------
+struct Prof {
+  bool on = false;
+  struct Pending { int id; cudaEvent_t a, b; double bytes, flops; };
+  std::vector<Pending> pend;
+  std::vector<bse_prof_entry> acc;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  int id_of(const char* name) {
+    for (size_t i = 0; i < acc.size(); ++i)
+      if (!strncmp(acc[i].name, name, sizeof(acc[i].name))) return (int)i;
+    bse_prof_entry e{};
+    strncpy(e.name, name, sizeof(e.name) - 1);
+    acc.push_back(e);
+    return (int)acc.size() - 1;
+  }
+  void resolve() {   // call after the stream has been synchronised
+    for (auto& p : pend) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) acc[p.id].ms += ms;
+      acc[p.id].calls += 1;
+      acc[p.id].bytes += p.bytes;
+      acc[p.id].flops += p.flops;
+      pool.push_back(p.a); pool.push_back(p.b);
+    }
+    pend.clear();
+  }
+  ~Prof() {
+    for (auto& p : pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 struct bse_ctx {
+  Prof prof;
   // problem
   int N = 0;
   long n3 = 0;
@@ -38,7 +79,7 @@ struct bse_ctx {
   float *psi32 = nullptr, *pdep32 = nullptr, *vloc32 = nullptr, *upsi32 = nullptr;
   // pairs / tau
   int *nbr_ptr = nullptr, *nbr_w = nullptr, *nbr_p = nullptr, *pv = nullptr, *pw = nullptr;
-  int64_t n_pairs = 0;
+  int64_t n_pairs = 0, nnz = 0;
   void* tau = nullptr;
   // operator workspace
   void *ws_a = nullptr, *ws_r = nullptr, *ws_h = nullptr, *ws_c = nullptr;
@@ -87,6 +128,23 @@ void dfree(bse_ctx* c, void* p) {
   if (it != c->allocs.end()) c->allocs.erase(it);
   cudaFree(p);
 }
+struct Scope {
+  bse_ctx* c; int id = -1; cudaEvent_t a = nullptr; double bytes, flops;
+  Scope(bse_ctx* c_, const char* name, double b, double f) : c(c_), bytes(b), flops(f) {
+    if (!c->prof.on) return;
+    id = c->prof.id_of(name);
+    a = c->prof.get();
+    cudaEventRecord(a, c->st);
+  }
+  ~Scope() {
+    if (id < 0) return;
+    cudaEvent_t b = c->prof.get();
+    cudaEventRecord(b, c->st);
+    c->prof.pend.push_back({id, a, b, bytes, flops});
+  }
+};
+inline double fft_flops(long n3, long grids) { return 5.0 * (double)n3 * std::log2((double)n3) * (double)grids; }
+
 #define CA(expr)                    \
   do {                              \
     int _r = (expr);                \
@@ -198,27 +256,54 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
     cplx<T>* ga = (cplx<T>*)c->ws_a;
     cplx<T>* gr = (cplx<T>*)c->ws_r;
     cplx<T>* gh = (cplx<T>*)c->ws_h;
+    const double sz = sizeof(T), gb = (double)ngr * n3 * sizeof(cplx<T>);
     // a_sv(G) -> a_sv(r)
-    CK((sphere_unpack<T, T>(ain, nf, c->n_pw, c->n_half, c->gpos, c->gneg, ga, n3, true, false, c->st)));
-    CK(fft3d<T>(ga, ngr, N, +1, tw_of<T>(c), c->st));
+    {
+      Scope sc(c, "sphere_unpack", (double)nf * c->n_pw * sz + gb, 0.0);
+      CK((sphere_unpack<T, T>(ain, nf, c->n_pw, c->n_half, c->gpos, c->gneg, ga, n3, true, false, c->st)));
+    }
+    {
+      Scope sc(c, "fft_inverse_a", 2.0 * gb, fft_flops(n3, ngr));
+      CK(fft3d<T>(ga, ngr, N, +1, tw_of<T>(c), c->st));
+    }
     // Hartree potential of the pair density sum_w psi_w a_sw (Eq. k1e)
     const long nh = (nv + 1) / 2;
     CK(cudaMemsetAsync(gh, 0, (size_t)nh * n3 * sizeof(cplx<T>), c->st));
     if (sf != 0.0) {
-      CK(hartree_density<T>((int)nv, c->n_occ, n3, (const T*)ga, upsi_of<T>(c), (T*)gh, c->st));
+      {
+        Scope sc(c, "hartree_density", ((double)nf + c->n_occ + nv) * n3 * sz, 2.0 * nf * n3);
+        CK(hartree_density<T>((int)nv, c->n_occ, n3, (const T*)ga, upsi_of<T>(c), (T*)gh, c->st));
+      }
+      Scope sc(c, "hartree_potential", 6.0 * nh * n3 * sizeof(cplx<T>), 2.0 * fft_flops(n3, nh));
       CK(fft3d<T>(gh, nh, N, -1, tw_of<T>(c), c->st));
       CK(grid_coulomb<T>(gh, nh, N, c->L, c->omega, 0, 1.0 / (double)n3, c->st));
       CK(fft3d<T>(gh, nh, N, +1, tw_of<T>(c), c->st));
     }
     // real-space combination with the screened direct term (Eq. k1d)
     if (nf & 1) CK(cudaMemsetAsync(gr + (ngr - 1) * n3, 0, (size_t)n3 * sizeof(cplx<T>), c->st));
-    CK(k1d_combine<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->nbr_ptr, c->nbr_w, c->nbr_p,
-                      vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
+    {
+      const double nnz = (double)c->nnz;
+      Scope sc(c, "k1d_combine",
+               ((double)c->n_pairs + 2.0 * nf + 1.0 + nv + c->n_occ) * n3 * sz,
+               (2.0 * nnz * nv + 5.0 * nf) * n3);
+      CK(k1d_combine<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->nbr_ptr, c->nbr_w, c->nbr_p,
+                        vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
+    }
     // back to the sphere, plus (1/2|G|^2 + Delta - eps_v) a (Eq. d)
-    CK(fft3d<T>(gr, ngr, N, -1, tw_of<T>(c), c->st));
-    CK((sphere_pack<T, T>(gr, nf, c->n_pw, c->n_half, c->gpos, c->gneg, n3, 1.0 / (double)n3, aout,
-                          ain, c->g2p, c->eps, c->scissor, c->n_occ, c->st)));
-    CA(project<T>(c, nf, aout, (T*)c->ws_c));
+    {
+      Scope sc(c, "fft_forward_r", 2.0 * gb, fft_flops(n3, ngr));
+      CK(fft3d<T>(gr, ngr, N, -1, tw_of<T>(c), c->st));
+    }
+    {
+      Scope sc(c, "sphere_pack_d", gb + 2.0 * nf * c->n_pw * sz, 4.0 * nf * c->n_pw);
+      CK((sphere_pack<T, T>(gr, nf, c->n_pw, c->n_half, c->gpos, c->gneg, n3, 1.0 / (double)n3, aout,
+                            ain, c->g2p, c->eps, c->scissor, c->n_occ, c->st)));
+    }
+    {
+      Scope sc(c, "projector_pc", (3.0 * nf * c->n_pw + (double)c->n_occ * c->n_pw) * sz,
+               4.0 * nf * c->n_occ * (double)c->n_pw);
+      CA(project<T>(c, nf, aout, (T*)c->ws_c));
+    }
   }
   return BSE_OK;
 }
@@ -264,6 +349,7 @@ int build_tau_impl(bse_ctx* c) {
       if (pid[v][w] >= 0) { nw.push_back(w); np.push_back(pid[v][w]); }
     ptr[v + 1] = (int)nw.size();
   }
+  c->nnz = (int64_t)nw.size();
   dfree(c, c->nbr_ptr); dfree(c, c->nbr_w); dfree(c, c->nbr_p); dfree(c, c->pv); dfree(c, c->pw);
   dfree(c, c->tau); c->tau = nullptr;
   CA(dalloc(c, &c->nbr_ptr, ptr.size()));
@@ -294,6 +380,9 @@ int build_tau_impl(bse_ctx* c) {
   for (long p0 = 0; p0 < c->n_pairs; p0 += nb) {
     const int b = (int)std::min<long>(nb, c->n_pairs - p0);
     const long ng = (b + 1) / 2;
+    const double gbt = (double)ng * n3 * sizeof(cplx<T>);
+    Scope sc(c, "tau_build", gbt * 8.0 + (double)b * n3 * sizeof(T),
+             2.0 * fft_flops(n3, ng) + 4.0 * b * (double)c->n_pdep * c->n_pw);
     CK(pair_product<T>(b, c->pv + p0, c->pw + p0, upsi_of<T>(c), n3, 1.0 / c->omega, grids, c->st));
     CK(fft3d<T>(grids, ng, c->N, -1, tw_of<T>(c), c->st));
     CK(grid_coulomb<T>(grids, ng, c->N, c->L, c->omega, 1, 1.0 / (double)n3, c->st));
@@ -444,9 +533,15 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
   int kk = 0;
   while (true) {
     ++it;
-    CK((gemm<T, double>(false, true, m, m, (int)dim, 1.0, V, dim, W, dim, 0.0, Hs, m, 0, c->st)));
-    CK(symmetrize(m, Hs, m, c->st));
-    CK(jacobi_eigh(m, Hs, m, jw, Yv, theta, info, c->st));
+    {
+      Scope sc(c, "davidson_rr", 2.0 * m * (double)dim * sizeof(T), 2.0 * m * m * (double)dim);
+      CK((gemm<T, double>(false, true, m, m, (int)dim, 1.0, V, dim, W, dim, 0.0, Hs, m, 0, c->st)));
+    }
+    {
+      Scope sc(c, "davidson_eigh", 16.0 * m * m, 0.0);
+      CK(symmetrize(m, Hs, m, c->st));
+      CK(jacobi_eigh(m, Hs, m, jw, Yv, theta, info, c->st));
+    }
     kk = std::min(ne, m);
     CK((convert<double, T>((long)m * m, Yv, Yt, c->st)));
     CK((gemm<T, T>(true, false, kk, (int)dim, m, 1.0, Yt, m, V, dim, 0.0, X, dim, 1, c->st)));
@@ -695,6 +790,8 @@ int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) 
 int bse_build_tau(bse_ctx* c, int64_t* n_pairs_out, double* thr_out) {
   if (!c) return BSE_ERR_INVALID_ARG;
   int r = (c->prec == BSE_PREC_FP64) ? build_tau_impl<double>(c) : build_tau_impl<float>(c);
+  cudaStreamSynchronize(c->st);
+  c->prof.resolve();
   if (r != BSE_OK) return r;
   if (n_pairs_out) *n_pairs_out = c->n_pairs;
   if (thr_out) *thr_out = c->thr;
@@ -727,6 +824,7 @@ int bse_apply_liouville(bse_ctx* c, int n_vec, const void* a_in, void* a_out) {
   if (r != BSE_OK) return r;
   cudaError_t e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return cuda_fail(c, e, "bse_apply_liouville");
+  c->prof.resolve();
   return BSE_OK;
 }
 
@@ -735,9 +833,38 @@ int bse_davidson(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, void
   if (!c) return BSE_ERR_INVALID_ARG;
   if (!o || !omega_out) return fail(c, BSE_ERR_INVALID_ARG, "null options or omega_out");
   if (!c->tau_ready) return fail(c, BSE_ERR_STATE, "bse_build_tau must run before bse_davidson");
-  return (c->prec == BSE_PREC_FP64)
-             ? davidson_impl<double>(c, o, omega_out, (double*)vec_out, stats)
-             : davidson_impl<float>(c, o, omega_out, (float*)vec_out, stats);
+  int r = (c->prec == BSE_PREC_FP64)
+              ? davidson_impl<double>(c, o, omega_out, (double*)vec_out, stats)
+              : davidson_impl<float>(c, o, omega_out, (float*)vec_out, stats);
+  cudaStreamSynchronize(c->st);
+  c->prof.resolve();
+  return r;
+}
+
+int bse_profile(bse_ctx* c, int mode) {
+  if (!c) return BSE_ERR_INVALID_ARG;
+  cudaStreamSynchronize(c->st);
+  c->prof.resolve();
+  if (mode == 1) c->prof.on = true;
+  else if (mode == 0) c->prof.on = false;
+  else if (mode == -1) c->prof.acc.clear();
+  else return fail(c, BSE_ERR_INVALID_ARG, "bse_profile mode must be 1, 0 or -1");
+  return BSE_OK;
+}
+
+int bse_profile_read(bse_ctx* c, bse_prof_entry* out, int cap, int* n_out, int64_t* launches) {
+  if (!c) {   // launch count only
+    if (n_out) *n_out = 0;
+    if (launches) *launches = (int64_t)launch_count();
+    return launches ? BSE_OK : BSE_ERR_INVALID_ARG;
+  }
+  cudaStreamSynchronize(c->st);
+  c->prof.resolve();
+  if (out)
+    for (int i = 0; i < cap && i < (int)c->prof.acc.size(); ++i) out[i] = c->prof.acc[i];
+  if (n_out) *n_out = (int)c->prof.acc.size();
+  if (launches) *launches = (int64_t)launch_count();
+  return BSE_OK;
 }
 
 }  // extern "C"

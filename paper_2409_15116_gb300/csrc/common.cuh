@@ -31,4 +31,10 @@ __device__ __forceinline__ size_t pair_off(long f, long r, long n3) {
   return (size_t)(f >> 1) * 2 * (size_t)n3 + 2 * (size_t)r + (size_t)(f & 1);
 }
 
+namespace bse {
+// count of kernel launches issued by this library (host side, all contexts)
+void note_launch();
+long long launch_count();
+}  // namespace bse
+
 __device__ __forceinline__ int iceil_div(int a, int b) { return (a + b - 1) / b; }

@@ -162,7 +162,7 @@ static cudaError_t launch_fft3d(cplx<T>* data, long n_batch, int sign, const cpl
   const long blocks = n_batch * (long)N * N / TX;
   if (blocks <= 0) return cudaSuccess;
   for (int axis = 0; axis < 3; ++axis) {
-    fft_axis_kernel<T, N><<<(unsigned)blocks, 256, smem, st>>>(data, axis, sign, table);
+    fft_axis_kernel<T, N><<<(unsigned)blocks, 256, smem, st>>>(data, axis, sign, table); note_launch();
   }
   return cudaGetLastError();
 }
@@ -299,7 +299,7 @@ cudaError_t sphere_unpack(const TI* P, long n_fields, int n_pw, int n_half, cons
   }
   const long total = n_c * n_half;
   sphere_unpack_kernel<T, TI><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
-      P, n_fields, n_pw, n_half, gpos, gneg, grids, n3, accumulate ? 1 : 0);
+      P, n_fields, n_pw, n_half, gpos, gneg, grids, n3, accumulate ? 1 : 0); note_launch();
   return cudaGetLastError();
 }
 
@@ -312,7 +312,7 @@ cudaError_t sphere_pack(const cplx<T>* grids, long n_fields, int n_pw, int n_hal
   const long total = n_c * n_half;
   if (total == 0) return cudaSuccess;
   sphere_pack_kernel<T, TO><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
-      grids, n_fields, n_pw, n_half, gpos, gneg, n3, scale, out, add_in, g2p, eps, shift, n_occ);
+      grids, n_fields, n_pw, n_half, gpos, gneg, n3, scale, out, add_in, g2p, eps, shift, n_occ); note_launch();
   return cudaGetLastError();
 }
 
@@ -353,7 +353,7 @@ cudaError_t grid_coulomb(cplx<T>* grids, long n_grids, int N, double L, double o
   const long total = n_grids * (long)N * N * N;
   if (total == 0) return cudaSuccess;
   grid_coulomb_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(grids, n_grids, N, L,
-                                                                         omega, mode, scale);
+                                                                         omega, mode, scale); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t grid_coulomb<float>(float2*, long, int, double, double, int, double, cudaStream_t);

@@ -131,19 +131,19 @@ static cudaError_t launch(int M, int N, int K, double alpha, const T* A, long ld
   int atomic = 0;
   if (splitk > 1) {
     const long tot = (long)M * N;
-    scale_matrix_kernel<TC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, C, ldc, beta);
+    scale_matrix_kernel<TC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, C, ldc, beta); note_launch();
     atomic = 1;
   }
   if (K == 0) {
     if (splitk <= 1) {
       const long tot = (long)M * N;
-      scale_matrix_kernel<TC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, C, ldc, beta);
+      scale_matrix_kernel<TC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, C, ldc, beta); note_launch();
     }
     return cudaGetLastError();
   }
   dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)splitk);
   gemm_kernel<T, TC, AT, BT, TM, TN, DFLUSH><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb,
-                                                                  beta, C, ldc, k_chunk, atomic);
+                                                                  beta, C, ldc, k_chunk, atomic); note_launch();
   return cudaGetLastError();
 }
 

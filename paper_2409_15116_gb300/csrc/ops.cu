@@ -2,9 +2,14 @@
 // Davidson solver.
 #include "common.cuh"
 #include "kernels.h"
+#include <atomic>
 #include <cmath>
 
 namespace bse {
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 static inline unsigned nblk(long total, int t = 256) { return (unsigned)((total + t - 1) / t); }
 
@@ -31,7 +36,7 @@ cudaError_t pair_product(int nb, const int* pv, const int* pw, const T* upsi, lo
                          cplx<T>* grids, cudaStream_t st) {
   const long tot = (long)((nb + 1) / 2) * n3;
   if (!tot) return cudaSuccess;
-  pair_product_kernel<T><<<nblk(tot), 256, 0, st>>>(nb, pv, pw, upsi, n3, (T)scale, grids);
+  pair_product_kernel<T><<<nblk(tot), 256, 0, st>>>(nb, pv, pw, upsi, n3, (T)scale, grids); note_launch();
   return cudaGetLastError();
 }
 
@@ -51,7 +56,7 @@ template <typename T>
 cudaError_t deinterleave_pairs(int nb, const cplx<T>* grids, long n3, T* tau, cudaStream_t st) {
   const long tot = (long)((nb + 1) / 2) * n3;
   if (!tot) return cudaSuccess;
-  deinterleave_kernel<T><<<nblk(tot), 256, 0, st>>>(nb, grids, n3, tau);
+  deinterleave_kernel<T><<<nblk(tot), 256, 0, st>>>(nb, grids, n3, tau); note_launch();
   return cudaGetLastError();
 }
 
@@ -69,7 +74,7 @@ __global__ void square_fields_kernel(int n, const double* __restrict__ u, long n
 cudaError_t square_fields(int n, const double* u, long n3, double* rho, cudaStream_t st) {
   const long tot = (long)n * n3;
   if (!tot) return cudaSuccess;
-  square_fields_kernel<<<nblk(tot), 256, 0, st>>>(n, u, n3, rho);
+  square_fields_kernel<<<nblk(tot), 256, 0, st>>>(n, u, n3, rho); note_launch();
   return cudaGetLastError();
 }
 
@@ -86,8 +91,8 @@ __global__ void normalize_overlap_kernel(int n, double* g, const double* d) {
 // O_vw = Gram_vw / sqrt(Gram_vv Gram_ww); the diagonal becomes exactly 1
 cudaError_t normalize_overlap(int n, double* gram, double* diag, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  overlap_diag_kernel<<<nblk(n), 256, 0, st>>>(n, gram, diag);
-  normalize_overlap_kernel<<<nblk((long)n * n), 256, 0, st>>>(n, gram, diag);
+  overlap_diag_kernel<<<nblk(n), 256, 0, st>>>(n, gram, diag); note_launch();
+  normalize_overlap_kernel<<<nblk((long)n * n), 256, 0, st>>>(n, gram, diag); note_launch();
   return cudaGetLastError();
 }
 
@@ -110,7 +115,7 @@ cudaError_t hartree_density(int n_vec, int n_occ, long n3, const T* a, const T* 
                             cudaStream_t st) {
   if (!n_vec) return cudaSuccess;
   dim3 grid(nblk(n3), n_vec);
-  hartree_density_kernel<T><<<grid, 256, 0, st>>>(n_vec, n_occ, n3, a, upsi, h);
+  hartree_density_kernel<T><<<grid, 256, 0, st>>>(n_vec, n_occ, n3, a, upsi, h); note_launch();
   return cudaGetLastError();
 }
 
@@ -161,7 +166,7 @@ cudaError_t k1d_combine(int n_vec, int n_occ, long n3, const T* a, const T* tau,
   if (!n_vec) return cudaSuccess;
   dim3 grid(nblk(n3), n_occ, (n_vec + SCH - 1) / SCH);
   k1d_combine_kernel<T, SCH><<<grid, 256, 0, st>>>(n_vec, n_occ, n3, a, tau, nbr_ptr, nbr_w, nbr_p,
-                                                   vloc, vh, upsi, (T)spin_factor, out);
+                                                   vloc, vh, upsi, (T)spin_factor, out); note_launch();
   return cudaGetLastError();
 }
 
@@ -179,7 +184,7 @@ template <typename T>
 cudaError_t scale_columns(int rows, int cols, T* C, long ldc, const double* f, cudaStream_t st) {
   const long tot = (long)rows * cols;
   if (!tot) return cudaSuccess;
-  scale_columns_kernel<T><<<nblk(tot), 256, 0, st>>>(rows, cols, C, ldc, f);
+  scale_columns_kernel<T><<<nblk(tot), 256, 0, st>>>(rows, cols, C, ldc, f); note_launch();
   return cudaGetLastError();
 }
 
@@ -191,7 +196,7 @@ __global__ void convert_kernel(long n, const TI* in, TO* out) {
 template <typename TI, typename TO>
 cudaError_t convert(long n, const TI* in, TO* out, cudaStream_t st) {
   if (!n) return cudaSuccess;
-  convert_kernel<TI, TO><<<nblk(n), 256, 0, st>>>(n, in, out);
+  convert_kernel<TI, TO><<<nblk(n), 256, 0, st>>>(n, in, out); note_launch();
   return cudaGetLastError();
 }
 
@@ -207,7 +212,7 @@ template <typename T>
 cudaError_t pair_grid_to_rows(int n, const T* grids, long n3, T* rows, cudaStream_t st) {
   const long tot = (long)n * n3;
   if (!tot) return cudaSuccess;
-  pair_grid_to_rows_kernel<T><<<nblk(tot), 256, 0, st>>>(n, grids, n3, rows);
+  pair_grid_to_rows_kernel<T><<<nblk(tot), 256, 0, st>>>(n, grids, n3, rows); note_launch();
   return cudaGetLastError();
 }
 
@@ -248,7 +253,7 @@ cudaError_t residuals(int k, long dim, const T* X, const T* LX, const double* th
   long nb = (dim + 255) / 256;
   if (nb > 592) nb = 592;
   dim3 grid((unsigned)nb, k);
-  residual_kernel<T><<<grid, 256, 0, st>>>(dim, X, LX, theta, R, norms2);
+  residual_kernel<T><<<grid, 256, 0, st>>>(dim, X, LX, theta, R, norms2); note_launch();
   return cudaGetLastError();
 }
 
@@ -271,12 +276,13 @@ cudaError_t row_norms2(int k, long dim, const T* X, double* norms2, cudaStream_t
   long nb = (dim + 255) / 256;
   if (nb > 592) nb = 592;
   dim3 grid((unsigned)nb, k);
-  row_norms2_kernel<T><<<grid, 256, 0, st>>>(dim, X, norms2);
+  row_norms2_kernel<T><<<grid, 256, 0, st>>>(dim, X, norms2); note_launch();
   return cudaGetLastError();
 }
 
-// diagonal preconditioner t = r / (d - theta), d = 1/2|G|^2 + V(0) + Delta - eps_v,
-// |d - theta| clamped to >= 1e-2 with its sign; the pad coordinate is set to 0
+// diagonal preconditioner t = r / max(d - theta, 0.1 Ha), d = 1/2|G|^2 + V(0) + Delta - eps_v.
+// The positive floor keeps the preconditioner positive definite: where d < theta the
+// diagonal carries no information about L - theta. The pad coordinate is set to 0.
 template <typename T>
 __global__ void precond_diag_kernel(int n_occ, int n_pw, const T* R, const double* theta,
                                     const int* which, const double* g2p, const double* eps,
@@ -288,7 +294,7 @@ __global__ void precond_diag_kernel(int n_occ, int n_pw, const T* R, const doubl
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < dim; e += (long)gridDim.x * blockDim.x) {
     const int v = (int)(e / n_pw), j = (int)(e - (long)v * n_pw);
     double den = 0.5 * g2p[j] + v0 + shift - eps[v] - th;
-    if (fabs(den) < 1e-2) den = den >= 0 ? 1e-2 : -1e-2;
+    if (den < 0.1) den = 0.1;
     out[t * dim + e] = (j == 1) ? (T)0 : (T)((double)R[(long)i * dim + e] / den);
   }
 }
@@ -301,7 +307,7 @@ cudaError_t precond_diag(int k, int n_occ, int n_pw, const T* R, const double* t
   long nb = (dim + 255) / 256;
   if (nb > 1184) nb = 1184;
   dim3 grid((unsigned)nb, k);
-  precond_diag_kernel<T><<<grid, 256, 0, st>>>(n_occ, n_pw, R, theta, which, g2p, eps, v0, shift, out);
+  precond_diag_kernel<T><<<grid, 256, 0, st>>>(n_occ, n_pw, R, theta, which, g2p, eps, v0, shift, out); note_launch();
   return cudaGetLastError();
 }
 
@@ -313,7 +319,7 @@ __global__ void zero_pad_kernel(int rows, int n_pw, T* X) {
 template <typename T>
 cudaError_t zero_pad_column(int rows, int n_pw, T* X, cudaStream_t st) {
   if (!rows) return cudaSuccess;
-  zero_pad_kernel<T><<<nblk(rows), 256, 0, st>>>(rows, n_pw, X);
+  zero_pad_kernel<T><<<nblk(rows), 256, 0, st>>>(rows, n_pw, X); note_launch();
   return cudaGetLastError();
 }
 
@@ -330,7 +336,7 @@ cudaError_t scale_rows(int k, long dim, T* X, const double* s, cudaStream_t st) 
   long nb = (dim + 255) / 256;
   if (nb > 1184) nb = 1184;
   dim3 grid((unsigned)nb, k);
-  scale_rows_kernel<T><<<grid, 256, 0, st>>>(dim, X, s);
+  scale_rows_kernel<T><<<grid, 256, 0, st>>>(dim, X, s); note_launch();
   return cudaGetLastError();
 }
 
@@ -340,7 +346,7 @@ template <typename T>
 cudaError_t set_unit(T* x, long dim, long idx, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(x, 0, sizeof(T) * dim, st);
   if (e != cudaSuccess) return e;
-  set_unit_kernel<T><<<1, 1, 0, st>>>(x, idx);
+  set_unit_kernel<T><<<1, 1, 0, st>>>(x, idx); note_launch();
   return cudaGetLastError();
 }
 
@@ -356,7 +362,7 @@ __global__ void symmetrize_kernel(int m, double* A, long lda) {
 cudaError_t symmetrize(int m, double* A, long lda, cudaStream_t st) {
   const long tot = (long)m * m;
   if (!tot) return cudaSuccess;
-  symmetrize_kernel<<<nblk(tot), 256, 0, st>>>(m, A, lda);
+  symmetrize_kernel<<<nblk(tot), 256, 0, st>>>(m, A, lda); note_launch();
   return cudaGetLastError();
 }
 
@@ -496,7 +502,7 @@ cudaError_t jacobi_eigh(int m, const double* A, long lda, double* work, double* 
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  jacobi_kernel<<<1, 512, smem, st>>>(m, A, lda, work, V, w, info);
+  jacobi_kernel<<<1, 512, smem, st>>>(m, A, lda, work, V, w, info); note_launch();
   return cudaGetLastError();
 }
 
@@ -562,7 +568,7 @@ cudaError_t cholesky_inverse(int b, const double* S, long lds, double* Linv, int
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  cholesky_kernel<<<1, 256, smem, st>>>(b, S, lds, Linv, info);
+  cholesky_kernel<<<1, 256, smem, st>>>(b, S, lds, Linv, info); note_launch();
   return cudaGetLastError();
 }
 
