@@ -157,10 +157,15 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     from synth import CONFIGS
     metric = "time_to_16_lowest_VEEs_1meV_vs_fp64_plain"
-    cfg_desc = {"workload": "medium: L=20 bohr, 72^3 grid, N_G=20479, N_occ=256, N_pdep=512, "
-                            "15% of pairs, 16 VEEs, Davidson block 32, mixed FP32/FP64",
-                "grid": 72, "n_occ": 256, "n_pdep": 512, "n_eig": N_EIG, "block": BLOCK,
-                "l2": "inputs larger than L2 (tau 7.4 GB, r-space workspace 24 GB)"}
+    probe = CONFIGS[args.config]()
+    n_g = 2 * probe.n_half - 1
+    cfg_desc = {"workload": f"{args.config}: L={probe.L:g} bohr, {probe.n_grid}^3 grid, N_G={n_g}, "
+                            f"N_occ={probe.n_occ}, N_pdep={probe.n_pdep}, 15% of pairs, {N_EIG} VEEs, "
+                            f"Davidson block {BLOCK}, mixed FP32/FP64",
+                "grid": probe.n_grid, "n_occ": probe.n_occ, "n_pdep": probe.n_pdep, "n_eig": N_EIG,
+                "block": BLOCK,
+                "l2": "inputs larger than L2 (tau and r-space workspaces exceed 129 MB)"}
+    del probe
 
     if args.impl == "reference":
         if rank != 0:

@@ -335,6 +335,9 @@ CONFIGS = {
     # mixed precision, medium: 72^3, 256 localised orbitals, 512 PDEP, 15% of pairs
     "medium": lambda s=None: make_localized(2 if s is None else s, 20.0, 72, 256, 2.5, 512,
                                             name="medium-L20-N72-occ256"),
+    # small profiling case of the same family: 48^3, 64 orbitals, 128 PDEP (~1 GB of fields)
+    "small": lambda s=None: make_localized(8 if s is None else s, 20.0 * 48 / 72, 48, 64, 2.5, 128,
+                                           name="small-L13.3-N48-occ64"),
     # one member of the uneven batch (seeds 300..363)
     "batch": lambda s=None: make_batched_member(300 if s is None else s),
     # large: 96^3, 1024 orbitals, 1024 PDEP, ~20k pairs
