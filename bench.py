@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--config", default="medium")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle sample")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     return ap.parse_args()
 
@@ -165,12 +166,11 @@ def main():
                 "grid": probe.n_grid, "n_occ": probe.n_occ, "n_pdep": probe.n_pdep, "n_eig": N_EIG,
                 "block": BLOCK,
                 "l2": "inputs larger than L2 (tau and r-space workspaces exceed 129 MB)"}
-    del probe
 
     if args.impl == "reference":
         if rank != 0:
             return
-        inst = CONFIGS[args.config]()
+        inst = probe
         vals = []
         for i in range(args.warmup + args.steps):
             r = cpu_oracle_sample(inst, n_apply_vectors=800, budget_s=args.cpu_budget)
@@ -199,7 +199,7 @@ def main():
     if world > 1:
         dist.barrier()
     from paper_2409_15116_gb300 import Context, PREC_MIXED, PREC_FP64, binding
-    inst = CONFIGS[args.config](None if rank == 0 else 1000 + rank)
+    inst = probe if rank == 0 else CONFIGS[args.config](1000 + rank)
     stream = torch.cuda.current_stream()
     ctx = Context(inst, PREC_MIXED, stream=stream.cuda_stream)
 
@@ -260,7 +260,7 @@ def main():
 
     # end-to-end through the C ABI with host buffers (context creation uploads the inputs)
     e2e = None
-    if rank == 0:
+    if rank == 0 and not args.no_e2e:
         h2d = sum(np.asarray(a).nbytes for a in (inst.miller, inst.psi, inst.eps, inst.v_loc,
                                                   inst.pdep, inst.lam))
         torch.cuda.synchronize()
