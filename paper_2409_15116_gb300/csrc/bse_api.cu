@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <queue>
 #include <string>
 #include <vector>
@@ -79,6 +80,10 @@ struct bse_ctx {
   float *psi32 = nullptr, *pdep32 = nullptr, *vloc32 = nullptr, *upsi32 = nullptr;
   // pairs / tau
   int *nbr_ptr = nullptr, *nbr_w = nullptr, *nbr_p = nullptr, *pv = nullptr, *pw = nullptr;
+  // row blocks of four orbitals: union of the rows' neighbours, pair index or -1 per row
+  int *bptr = nullptr, *bw = nullptr;
+  int4* bp = nullptr;
+  int n_rblocks = 0;
   int64_t n_pairs = 0, nnz = 0;
   void* tau = nullptr;
   // operator workspace
@@ -286,8 +291,13 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
       Scope sc(c, "k1d_combine",
                ((double)c->n_pairs + 2.0 * nf + 1.0 + nv + c->n_occ) * n3 * sz,
                (2.0 * nnz * nv + 5.0 * nf) * n3);
-      CK(k1d_combine<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->nbr_ptr, c->nbr_w, c->nbr_p,
-                        vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
+      if (k1d_vectors_per_cta<T>(c->n_occ) > 0 && n3 % 16 == 0) {
+        CK(k1d_tiled<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->bptr, c->bw, c->bp,
+                        c->n_rblocks, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
+      } else {
+        CK(k1d_combine<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->nbr_ptr, c->nbr_w, c->nbr_p,
+                          vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
+      }
     }
     // back to the sphere, plus (1/2|G|^2 + Delta - eps_v) a (Eq. d)
     {
@@ -350,11 +360,36 @@ int build_tau_impl(bse_ctx* c) {
     ptr[v + 1] = (int)nw.size();
   }
   c->nnz = (int64_t)nw.size();
+  // block-CSR over row blocks of 4 consecutive orbitals
+  std::vector<int> hbptr(1, 0), hbw;
+  std::vector<int4> hbp;
+  const int nrb = (n + 3) / 4;
+  for (int b = 0; b < nrb; ++b) {
+    for (int w = 0; w < n; ++w) {
+      int4 q; q.x = q.y = q.z = q.w = -1;
+      bool any = false;
+      int* qq = &q.x;
+      for (int i = 0; i < 4; ++i) {
+        const int v = 4 * b + i;
+        if (v < n && pid[v][w] >= 0) { qq[i] = pid[v][w]; any = true; }
+      }
+      if (any) { hbw.push_back(w); hbp.push_back(q); }
+    }
+    hbptr.push_back((int)hbw.size());
+  }
+  c->n_rblocks = nrb;
   dfree(c, c->nbr_ptr); dfree(c, c->nbr_w); dfree(c, c->nbr_p); dfree(c, c->pv); dfree(c, c->pw);
   dfree(c, c->tau); c->tau = nullptr;
   CA(dalloc(c, &c->nbr_ptr, ptr.size()));
   CA(dalloc(c, &c->nbr_w, nw.size()));
   CA(dalloc(c, &c->nbr_p, np.size()));
+  dfree(c, c->bptr); dfree(c, c->bw); dfree(c, c->bp);
+  CA(dalloc(c, &c->bptr, hbptr.size()));
+  CA(dalloc(c, &c->bw, hbw.size()));
+  CA(dalloc(c, &c->bp, hbp.size()));
+  CK(cudaMemcpyAsync(c->bptr, hbptr.data(), sizeof(int) * hbptr.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->bw, hbw.data(), sizeof(int) * hbw.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->bp, hbp.data(), sizeof(int4) * hbp.size(), cudaMemcpyHostToDevice, c->st));
   CA(dalloc(c, &c->pv, c->pv_h.size()));
   CA(dalloc(c, &c->pw, c->pw_h.size()));
   CK(cudaMemcpyAsync(c->nbr_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, c->st));
@@ -527,6 +562,12 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
   }
   if (m == 0) return fail(c, BSE_ERR_NUMERIC, "no initial vector survives the projection");
   CA(timed_apply(m, V, W));
+  // Rayleigh-Ritz matrix Hs = V W^T kept with leading dimension ms and updated by columns
+  {
+    Scope sc(c, "davidson_rr", 2.0 * m * (double)dim * sizeof(T), 2.0 * m * m * (double)dim);
+    CK((gemm<T, double>(false, true, m, m, (int)dim, 1.0, V, dim, W, dim, 0.0, Hs, ms, 0, c->st)));
+    CK(symmetrize(m, Hs, ms, c->st));
+  }
   int it = 0;
   bool converged = false;
   std::vector<double> th(ms), rn(ms);
@@ -534,19 +575,18 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
   while (true) {
     ++it;
     {
-      Scope sc(c, "davidson_rr", 2.0 * m * (double)dim * sizeof(T), 2.0 * m * m * (double)dim);
-      CK((gemm<T, double>(false, true, m, m, (int)dim, 1.0, V, dim, W, dim, 0.0, Hs, m, 0, c->st)));
-    }
-    {
       Scope sc(c, "davidson_eigh", 16.0 * m * m, 0.0);
-      CK(symmetrize(m, Hs, m, c->st));
-      CK(jacobi_eigh(m, Hs, m, jw, Yv, theta, info, c->st));
+      CK(jacobi_eigh(m, Hs, ms, jw, Yv, theta, info, c->st));
     }
     kk = std::min(ne, m);
-    CK((convert<double, T>((long)m * m, Yv, Yt, c->st)));
-    CK((gemm<T, T>(true, false, kk, (int)dim, m, 1.0, Yt, m, V, dim, 0.0, X, dim, 1, c->st)));
-    CK((gemm<T, T>(true, false, kk, (int)dim, m, 1.0, Yt, m, W, dim, 0.0, LX, dim, 1, c->st)));
-    CK(residuals<T>(kk, dim, X, LX, theta, Rr, nrm, c->st));
+    {
+      Scope sc(c, "davidson_ritz", 2.0 * (2.0 * m + 3.0 * kk) * (double)dim * sizeof(T),
+               4.0 * kk * m * (double)dim);
+      CK((convert<double, T>((long)m * m, Yv, Yt, c->st)));
+      CK((gemm<T, T>(true, false, kk, (int)dim, m, 1.0, Yt, m, V, dim, 0.0, X, dim, 1, c->st)));
+      CK((gemm<T, T>(true, false, kk, (int)dim, m, 1.0, Yt, m, W, dim, 0.0, LX, dim, 1, c->st)));
+      CK(residuals<T>(kk, dim, X, LX, theta, Rr, nrm, c->st));
+    }
     CK(cudaMemcpyAsync(th.data(), theta, sizeof(double) * kk, cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemcpyAsync(rn.data(), nrm, sizeof(double) * kk, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
@@ -562,9 +602,12 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
     int nt = (int)todo.size();
     if (nt == 0) break;
     CK(cudaMemcpyAsync(which, todo.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, c->st));
-    CK(precond_diag<T>(nt, c->n_occ, c->n_pw, Rr, theta, which, c->g2p, c->eps, c->v0, c->scissor,
-                       Tt, c->st));
-    CA(proj(nt, Tt));
+    {
+      Scope sc(c, "davidson_precond", 2.0 * nt * (double)dim * sizeof(T), 4.0 * nt * c->n_occ * (double)dim);
+      CK(precond_diag<T>(nt, c->n_occ, c->n_pw, Rr, theta, which, c->g2p, c->eps, c->v0, c->scissor,
+                         Tt, c->st));
+      CA(proj(nt, Tt));
+    }
     if (m + nt > ms) {
       const int kp = std::min(keep, m);
       CK((gemm<T, T>(true, false, kp, (int)dim, m, 1.0, Yt, m, V, dim, 0.0, S1, dim, 1, c->st)));
@@ -572,8 +615,13 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
       CK(cudaMemcpyAsync(V, S1, sizeof(T) * kp * dim, cudaMemcpyDeviceToDevice, c->st));
       CK(cudaMemcpyAsync(W, S2, sizeof(T) * kp * dim, cudaMemcpyDeviceToDevice, c->st));
       m = kp;
+      Scope sc(c, "davidson_rr", 2.0 * m * (double)dim * sizeof(T), 2.0 * m * m * (double)dim);
+      CK((gemm<T, double>(false, true, m, m, (int)dim, 1.0, V, dim, W, dim, 0.0, Hs, ms, 0, c->st)));
+      CK(symmetrize(m, Hs, ms, c->st));
     }
     // CGS2 against V, dropping directions that lose all but 1e-8 of their norm
+    std::unique_ptr<Scope> sc_orth(new Scope(c, "davidson_orth", (4.0 * m + 8.0 * nt) * (double)dim * sizeof(T),
+                                             8.0 * m * nt * (double)dim + 4.0 * nt * nt * (double)dim));
     std::vector<double> n0(nt), n1(nt);
     CK(row_norms2<T>(nt, dim, Tt, nrm, c->st));
     CK(cudaMemcpyAsync(n0.data(), nrm, sizeof(double) * nt, cudaMemcpyDeviceToHost, c->st));
@@ -621,8 +669,16 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
       std::swap(Tt, Tt2);
     }
     if (nt == 0) break;
+    sc_orth.reset();
     CK(cudaMemcpyAsync(V + (long)m * dim, Tt, sizeof(T) * nt * dim, cudaMemcpyDeviceToDevice, c->st));
     CA(timed_apply(nt, V + (long)m * dim, W + (long)m * dim));
+    {
+      Scope sc(c, "davidson_rr", (m + 2.0 * nt) * (double)dim * sizeof(T),
+               2.0 * (m + nt) * nt * (double)dim);
+      CK((gemm<T, double>(false, true, m + nt, nt, (int)dim, 1.0, V, dim, W + (long)m * dim, dim,
+                          0.0, Hs + m, ms, 0, c->st)));
+      CK(mirror_new(Hs, ms, m, m + nt, c->st));
+    }
     m += nt;
   }
   for (int i = 0; i < ne; ++i) omega_out[i] = i < kk ? th[i] : NAN;

@@ -147,16 +147,29 @@ static cudaError_t launch(int M, int N, int K, double alpha, const T* A, long ld
   return cudaGetLastError();
 }
 
-template <typename T, typename TC>
-cudaError_t gemm(bool at, bool bt, int M, int N, int K, double alpha, const T* A, long lda,
-                 const T* B, long ldb, double beta, TC* C, long ldc, int splitk, cudaStream_t st) {
+template <typename T, typename TC, int TM, int TN>
+static cudaError_t dispatch_t(bool at, bool bt, int M, int N, int K, double alpha, const T* A,
+                              long lda, const T* B, long ldb, double beta, TC* C, long ldc,
+                              int splitk, cudaStream_t st) {
   constexpr bool DF = sizeof(T) < sizeof(TC);
-  constexpr int TM = sizeof(T) == 8 ? 4 : 4;
-  constexpr int TN = sizeof(T) == 8 ? 4 : 4;
   if (!at && bt) return launch<T, TC, false, true, TM, TN, DF>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk, st);
   if (!at && !bt) return launch<T, TC, false, false, TM, TN, DF>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk, st);
   if (at && !bt) return launch<T, TC, true, false, TM, TN, DF>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk, st);
   return launch<T, TC, true, true, TM, TN, DF>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk, st);
+}
+
+// Tile shape follows the operands: a side of at most 16 gets a 16-wide tile, so the
+// tall-skinny products of the Davidson algebra (16-32 rows against millions of
+// columns) do not pad a 64-wide tile.
+template <typename T, typename TC>
+cudaError_t gemm(bool at, bool bt, int M, int N, int K, double alpha, const T* A, long lda,
+                 const T* B, long ldb, double beta, TC* C, long ldc, int splitk, cudaStream_t st) {
+  const bool sm = M <= 16, sn = N <= 16;
+  if (sm && !sn) return dispatch_t<T, TC, 1, 4>(at, bt, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk, st);
+  if (sn && !sm) return dispatch_t<T, TC, 4, 1>(at, bt, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk, st);
+  if (sm && sn) return dispatch_t<T, TC, 1, 1>(at, bt, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk, st);
+  if (M <= 32 || N <= 32) return dispatch_t<T, TC, 2, 2>(at, bt, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk, st);
+  return dispatch_t<T, TC, 4, 4>(at, bt, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk, st);
 }
 
 template cudaError_t gemm<double, double>(bool, bool, int, int, int, double, const double*, long, const double*, long, double, double*, long, int, cudaStream_t);

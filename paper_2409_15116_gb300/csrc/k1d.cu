@@ -1,0 +1,172 @@
+// Screened direct term K1d of Eq. (k1d), fused with the real-space parts of D (Eq. d)
+// and K1e (Eq. k1e):
+//
+//   u_R,sv(r) = V_loc(r) u_a,sv(r) + s V_H,s(r) u_psi,v(r) - sum_{w in nbr(v)} tau_vw(r) u_a,sw(r)
+//
+// At each grid point the sum is a sparse (N_occ x N_occ) times dense (N_occ x n_vec)
+// product whose sparse factor tau(r) changes from point to point. A CTA owns a tile of
+// TR consecutive points and a chunk of SC trial vectors: it stages a(r) for every orbital
+// of the chunk in shared memory (read from HBM once, 128-byte rows), then streams tau
+// through rows grouped four at a time (one localisation site): each tau value is
+// loaded once per tile and reused for the SC vectors, each staged a value feeds the
+// four rows of a block. tau_vw(r) for pairs outside the overlap list is simply absent
+// (Eq. overlap); blocks list the union of their rows' neighbours with -1 for the
+// missing entries.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace bse {
+
+template <typename T, int TR, int SC>
+__global__ void __launch_bounds__(256) k1d_tile_kernel(
+    int n_vec, int n_occ, long n3, const T* __restrict__ a, const T* __restrict__ tau,
+    const int* __restrict__ bptr, const int* __restrict__ bw, const int4* __restrict__ bp,
+    int n_blocks, const T* __restrict__ vloc, const T* __restrict__ vh,
+    const T* __restrict__ upsi, T sf, T* __restrict__ out) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char k1d_smem[];
+  T* A = reinterpret_cast<T*>(k1d_smem);            // [n_occ][SC][TR]
+  T* VH = A + (size_t)n_occ * SC * TR;               // [SC][TR]
+  const int n_sc = (n_vec + SC - 1) / SC;
+  const int sc = blockIdx.x % n_sc;
+  const long tile = blockIdx.x / n_sc;
+  const long r0 = tile * TR;
+  const int s0 = sc * SC;
+  const int ns = min(SC, n_vec - s0);
+  const int tid = threadIdx.x;
+  // stage a(f, r0 .. r0+TR) for the fields f of this vector chunk
+  const long f_lo = (long)s0 * n_occ, f_hi = (long)(s0 + ns) * n_occ;
+  const long c_lo = f_lo >> 1, c_hi = (f_hi + 1) >> 1;
+  const C* ac = reinterpret_cast<const C*>(a);
+  for (long e = tid; e < (c_hi - c_lo) * TR; e += blockDim.x) {
+    const long c = c_lo + e / TR;
+    const int t = (int)(e % TR);
+    const C z = ac[c * n3 + r0 + t];
+    const long f0 = 2 * c, f1 = f0 + 1;
+    if (f0 >= f_lo) {
+      const long q = f0 - f_lo;
+      A[((q % n_occ) * SC + q / n_occ) * TR + t] = z.x;
+    }
+    if (f1 < f_hi) {
+      const long q = f1 - f_lo;
+      A[((q % n_occ) * SC + q / n_occ) * TR + t] = z.y;
+    }
+  }
+  for (int e = tid; e < SC * TR; e += blockDim.x) {
+    const int s = e / TR, t = e % TR;
+    VH[e] = (s < ns) ? vh[pair_off<T>(s0 + s, r0 + t, n3)] : (T)0;
+  }
+  __syncthreads();
+  const int t = tid % TR, g = tid / TR, G = blockDim.x / TR;
+  const long r = r0 + t;
+  const T vl = vloc[r];
+  for (int rb = g; rb < n_blocks; rb += G) {
+    T acc[4][SC];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int s = 0; s < SC; ++s) acc[i][s] = (T)0;
+    const int e0 = bptr[rb], e1 = bptr[rb + 1];
+    // one-deep software pipeline on the tau loads
+    int wn = 0;
+    T tn0 = 0, tn1 = 0, tn2 = 0, tn3 = 0;
+    if (e0 < e1) {
+      const int4 p = bp[e0];
+      wn = bw[e0];
+      tn0 = p.x >= 0 ? tau[(long)p.x * n3 + r] : (T)0;
+      tn1 = p.y >= 0 ? tau[(long)p.y * n3 + r] : (T)0;
+      tn2 = p.z >= 0 ? tau[(long)p.z * n3 + r] : (T)0;
+      tn3 = p.w >= 0 ? tau[(long)p.w * n3 + r] : (T)0;
+    }
+    for (int e = e0; e < e1; ++e) {
+      const int w = wn;
+      const T t0 = tn0, t1 = tn1, t2 = tn2, t3 = tn3;
+      if (e + 1 < e1) {
+        const int4 p = bp[e + 1];
+        wn = bw[e + 1];
+        tn0 = p.x >= 0 ? tau[(long)p.x * n3 + r] : (T)0;
+        tn1 = p.y >= 0 ? tau[(long)p.y * n3 + r] : (T)0;
+        tn2 = p.z >= 0 ? tau[(long)p.z * n3 + r] : (T)0;
+        tn3 = p.w >= 0 ? tau[(long)p.w * n3 + r] : (T)0;
+      }
+      const T* Aw = A + (size_t)w * SC * TR + t;
+#pragma unroll
+      for (int s = 0; s < SC; ++s) {
+        const T av = Aw[s * TR];
+        acc[0][s] = fma(t0, av, acc[0][s]);
+        acc[1][s] = fma(t1, av, acc[1][s]);
+        acc[2][s] = fma(t2, av, acc[2][s]);
+        acc[3][s] = fma(t3, av, acc[3][s]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int v = 4 * rb + i;
+      if (v >= n_occ) break;
+      const T up = upsi[pair_off<T>(v, r, n3)];
+      const T* Av = A + (size_t)v * SC * TR + t;
+#pragma unroll
+      for (int s = 0; s < SC; ++s) {
+        if (s >= ns) break;
+        const long f = (long)(s0 + s) * n_occ + v;
+        out[pair_off<T>(f, r, n3)] = vl * Av[s * TR] + sf * VH[s * TR + t] * up - acc[i][s];
+      }
+    }
+  }
+}
+
+template <typename T, int TR, int SC>
+static cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T* tau,
+                              const int* bptr, const int* bw, const int4* bp, int n_blocks,
+                              const T* vloc, const T* vh, const T* upsi, double sf, T* out,
+                              cudaStream_t st) {
+  const size_t smem = ((size_t)n_occ * SC * TR + SC * TR) * sizeof(T);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k1d_tile_kernel<T, TR, SC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const long tiles = n3 / TR;
+  const long blocks = tiles * ((n_vec + SC - 1) / SC);
+  k1d_tile_kernel<T, TR, SC><<<(unsigned)blocks, 256, smem, st>>>(
+      n_vec, n_occ, n3, a, tau, bptr, bw, bp, n_blocks, vloc, vh, upsi, (T)sf, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// shared-memory budget of the a(r) stage; SC (vectors per CTA) is the largest power of
+// two with n_occ * SC * TR * sizeof(T) within it
+constexpr size_t K1D_SMEM_BUDGET = 160 * 1024;
+
+template <typename T>
+int k1d_vectors_per_cta(int n_occ) {
+  constexpr int TR = 16;
+  for (int sc = 8; sc >= 1; sc >>= 1)
+    if ((size_t)n_occ * sc * TR * sizeof(T) + sc * TR * sizeof(T) <= K1D_SMEM_BUDGET) return sc;
+  return 0;
+}
+
+template <typename T>
+cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, const int* bptr,
+                      const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
+                      const T* upsi, double sf, T* out, cudaStream_t st) {
+  constexpr int TR = 16;
+  if (n_vec <= 0) return cudaSuccess;
+  if (n3 % TR) return cudaErrorInvalidValue;
+  switch (k1d_vectors_per_cta<T>(n_occ)) {
+    case 8: return launch_k1d<T, TR, 8>(n_vec, n_occ, n3, a, tau, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, out, st);
+    case 4: return launch_k1d<T, TR, 4>(n_vec, n_occ, n3, a, tau, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, out, st);
+    case 2: return launch_k1d<T, TR, 2>(n_vec, n_occ, n3, a, tau, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, out, st);
+    case 1: return launch_k1d<T, TR, 1>(n_vec, n_occ, n3, a, tau, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, out, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t k1d_tiled<float>(int, int, long, const float*, const float*, const int*, const int*, const int4*, int, const float*, const float*, const float*, double, float*, cudaStream_t);
+template cudaError_t k1d_tiled<double>(int, int, long, const double*, const double*, const int*, const int*, const int4*, int, const double*, const double*, const double*, double, double*, cudaStream_t);
+template int k1d_vectors_per_cta<float>(int);
+template int k1d_vectors_per_cta<double>(int);
+
+}  // namespace bse

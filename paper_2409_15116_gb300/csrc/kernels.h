@@ -45,6 +45,13 @@ template <typename T>
 cudaError_t k1d_combine(int n_vec, int n_occ, long n3, const T* a, const T* tau, const int* nbr_ptr,
                         const int* nbr_w, const int* nbr_p, const T* vloc, const T* vh,
                         const T* upsi, double spin_factor, T* out, cudaStream_t st);
+// ---- k1d.cu ----
+template <typename T>
+int k1d_vectors_per_cta(int n_occ);
+template <typename T>
+cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, const int* bptr,
+                      const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
+                      const T* upsi, double sf, T* out, cudaStream_t st);
 template <typename T>
 cudaError_t scale_columns(int rows, int cols, T* C, long ldc, const double* f, cudaStream_t st);
 template <typename TI, typename TO>
@@ -67,6 +74,7 @@ cudaError_t scale_rows(int k, long dim, T* X, const double* s, cudaStream_t st);
 template <typename T>
 cudaError_t set_unit(T* x, long dim, long idx, cudaStream_t st);
 cudaError_t symmetrize(int m, double* A, long lda, cudaStream_t st);
+cudaError_t mirror_new(double* A, long lda, int m0, int m1, cudaStream_t st);
 cudaError_t jacobi_eigh(int m, const double* A, long lda, double* work, double* V, double* w,
                         int* info, cudaStream_t st);
 cudaError_t cholesky_inverse(int b, const double* S, long lds, double* Linv, int* info,

@@ -359,6 +359,28 @@ __global__ void symmetrize_kernel(int m, double* A, long lda) {
   A[(long)i * lda + j] = v;
   A[(long)j * lda + i] = v;
 }
+// after columns [m0, m1) of the upper block were computed: copy them to the rows,
+// averaging inside the new diagonal block
+__global__ void mirror_new_kernel(double* A, long lda, int m0, int m1) {
+  const int nn = m1 - m0;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)m1 * nn) return;
+  const int i = (int)(idx / nn), j = m0 + (int)(idx - (long)i * nn);
+  if (i < m0) {
+    A[(long)j * lda + i] = A[(long)i * lda + j];
+  } else if (i < j) {
+    const double v = 0.5 * (A[(long)i * lda + j] + A[(long)j * lda + i]);
+    A[(long)i * lda + j] = v;
+    A[(long)j * lda + i] = v;
+  }
+}
+cudaError_t mirror_new(double* A, long lda, int m0, int m1, cudaStream_t st) {
+  const long tot = (long)m1 * (m1 - m0);
+  if (tot <= 0) return cudaSuccess;
+  mirror_new_kernel<<<nblk(tot), 256, 0, st>>>(A, lda, m0, m1); note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t symmetrize(int m, double* A, long lda, cudaStream_t st) {
   const long tot = (long)m * m;
   if (!tot) return cudaSuccess;
