@@ -209,10 +209,9 @@ __global__ void sphere_unpack_kernel(const TI* __restrict__ P, long n_fields, in
                                      cplx<T>* __restrict__ grids, long n3, int accumulate) {
   using C = cplx<T>;
   const long n_c = (n_fields + 1) / 2;
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n_c * n_half) return;
-  const long c = idx / n_half;
-  const int k = (int)(idx - c * n_half);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_half) return;
+  for (long c = blockIdx.y; c < n_c; c += gridDim.y) {
   const long fa = 2 * c, fb = 2 * c + 1;
   const bool hb = fb < n_fields;
   const T a0 = (T)P[fa * n_pw + 2 * k], a1 = (T)P[fa * n_pw + 2 * k + 1];
@@ -222,7 +221,7 @@ __global__ void sphere_unpack_kernel(const TI* __restrict__ P, long n_fields, in
     C F; F.x = a0; F.y = b0;
     if (accumulate) F = cadd(g[gpos[0]], F);
     g[gpos[0]] = F;
-    return;
+    continue;
   }
   const T s = (T)0.70710678118654752440;
   // cA = (a0 + i a1)/sqrt2, cB = (b0 + i b1)/sqrt2
@@ -233,6 +232,7 @@ __global__ void sphere_unpack_kernel(const TI* __restrict__ P, long n_fields, in
   if (accumulate) { Fp = cadd(g[gpos[k]], Fp); Fm = cadd(g[gneg[k]], Fm); }
   g[gpos[k]] = Fp;
   g[gneg[k]] = Fm;
+  }
 }
 
 // packed fields 2c, 2c+1 <- scale * grids[c] on the sphere (Hermitian separation), plus
@@ -246,10 +246,9 @@ __global__ void sphere_pack_kernel(const cplx<T>* __restrict__ grids, long n_fie
                                    double shift, int n_occ) {
   using C = cplx<T>;
   const long n_c = (n_fields + 1) / 2;
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n_c * n_half) return;
-  const long c = idx / n_half;
-  const int k = (int)(idx - c * n_half);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_half) return;
+  for (long c = blockIdx.y; c < n_c; c += gridDim.y) {
   const C* g = grids + c * n3;
   const T sc = (T)scale;
   C Fp = g[gpos[k]];
@@ -285,6 +284,7 @@ __global__ void sphere_pack_kernel(const cplx<T>* __restrict__ grids, long n_fie
     out[fb * n_pw + j0] = (TO)b0;
     out[fb * n_pw + j1] = (TO)b1;
   }
+  }
 }
 
 template <typename T, typename TI>
@@ -297,8 +297,8 @@ cudaError_t sphere_unpack(const TI* P, long n_fields, int n_pw, int n_half, cons
     cudaError_t e = cudaMemsetAsync(grids, 0, (size_t)n_c * n3 * sizeof(cplx<T>), st);
     if (e != cudaSuccess) return e;
   }
-  const long total = n_c * n_half;
-  sphere_unpack_kernel<T, TI><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+  dim3 grid((unsigned)((n_half + 255) / 256), (unsigned)(n_c < 65535 ? n_c : 65535));
+  sphere_unpack_kernel<T, TI><<<grid, 256, 0, st>>>(
       P, n_fields, n_pw, n_half, gpos, gneg, grids, n3, accumulate ? 1 : 0); note_launch();
   return cudaGetLastError();
 }
@@ -309,9 +309,9 @@ cudaError_t sphere_pack(const cplx<T>* grids, long n_fields, int n_pw, int n_hal
                         const double* g2p, const double* eps, double shift, int n_occ,
                         cudaStream_t st) {
   const long n_c = (n_fields + 1) / 2;
-  const long total = n_c * n_half;
-  if (total == 0) return cudaSuccess;
-  sphere_pack_kernel<T, TO><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+  if (n_c == 0) return cudaSuccess;
+  dim3 grid((unsigned)((n_half + 255) / 256), (unsigned)(n_c < 65535 ? n_c : 65535));
+  sphere_pack_kernel<T, TO><<<grid, 256, 0, st>>>(
       grids, n_fields, n_pw, n_half, gpos, gneg, n3, scale, out, add_in, g2p, eps, shift, n_occ); note_launch();
   return cudaGetLastError();
 }
@@ -330,11 +330,10 @@ template cudaError_t sphere_pack<float, float>(const float2*, long, int, int, co
 template <typename T>
 __global__ void grid_coulomb_kernel(cplx<T>* __restrict__ grids, long n_grids, int N, double L,
                                     double omega, int mode, double scale) {
-  const long n3 = (long)N * N * N;
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n_grids * n3) return;
-  const long r = idx % n3;
-  const int x = (int)(r % N), y = (int)((r / N) % N), z = (int)(r / ((long)N * N));
+  const int n3 = N * N * N;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n3) return;
+  const int x = r % N, y = (r / N) % N, z = r / (N * N);
   const int nx = x < N / 2 ? x : x - N, ny = y < N / 2 ? y : y - N, nz = z < N / 2 ? z : z - N;
   const double g = 6.283185307179586476925286766559 / L;
   const double g2 = g * g * (double)(nx * nx + ny * ny + nz * nz);
@@ -342,17 +341,20 @@ __global__ void grid_coulomb_kernel(cplx<T>* __restrict__ grids, long n_grids, i
   if (g2 > 0) f = (mode == 0) ? 12.566370614359172953850573533118 / (g2 * omega)
                               : 3.5449077018110320545963349666823 / sqrt(g2);
   f *= scale;
-  cplx<T> v = grids[idx];
-  v.x = (T)(v.x * f); v.y = (T)(v.y * f);
-  grids[idx] = v;
+  for (long b = blockIdx.y; b < n_grids; b += gridDim.y) {
+    cplx<T> v = grids[b * n3 + r];
+    v.x = (T)(v.x * f); v.y = (T)(v.y * f);
+    grids[b * n3 + r] = v;
+  }
 }
 
 template <typename T>
 cudaError_t grid_coulomb(cplx<T>* grids, long n_grids, int N, double L, double omega, int mode,
                          double scale, cudaStream_t st) {
-  const long total = n_grids * (long)N * N * N;
-  if (total == 0) return cudaSuccess;
-  grid_coulomb_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(grids, n_grids, N, L,
+  if (n_grids == 0) return cudaSuccess;
+  const long n3 = (long)N * N * N;
+  dim3 grid((unsigned)((n3 + 255) / 256), (unsigned)(n_grids < 65535 ? n_grids : 65535));
+  grid_coulomb_kernel<T><<<grid, 256, 0, st>>>(grids, n_grids, N, L,
                                                                          omega, mode, scale); note_launch();
   return cudaGetLastError();
 }

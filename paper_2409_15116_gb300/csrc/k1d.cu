@@ -38,18 +38,34 @@ __global__ void __launch_bounds__(256) k1d_tile_kernel(
   const long f_lo = (long)s0 * n_occ, f_hi = (long)(s0 + ns) * n_occ;
   const long c_lo = f_lo >> 1, c_hi = (f_hi + 1) >> 1;
   const C* ac = reinterpret_cast<const C*>(a);
-  for (long e = tid; e < (c_hi - c_lo) * TR; e += blockDim.x) {
-    const long c = c_lo + e / TR;
-    const int t = (int)(e % TR);
-    const C z = ac[c * n3 + r0 + t];
-    const long f0 = 2 * c, f1 = f0 + 1;
-    if (f0 >= f_lo) {
-      const long q = f0 - f_lo;
-      A[((q % n_occ) * SC + q / n_occ) * TR + t] = z.x;
+  if ((n_occ & 1) == 0) {
+    // even N_occ: complex grid c holds orbitals (2k, 2k+1) of one vector; a warp moves
+    // two 128-byte rows (16 complex values each) per iteration, no per-element division
+    const int half = n_occ >> 1;
+    const int rows = ns * half;
+    const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int sub = lane / TR, t = lane % TR;        // TR divides 32
+    constexpr int RPW = 32 / TR;                     // rows per warp pass
+    for (int row = wid * RPW + sub; row < rows; row += nw * RPW) {
+      const int sl = row / half, k = row - sl * half;
+      const C z = ac[(c_lo + row) * n3 + r0 + t];
+      A[((2 * k) * SC + sl) * TR + t] = z.x;
+      A[((2 * k + 1) * SC + sl) * TR + t] = z.y;
     }
-    if (f1 < f_hi) {
-      const long q = f1 - f_lo;
-      A[((q % n_occ) * SC + q / n_occ) * TR + t] = z.y;
+  } else {
+    for (long e = tid; e < (c_hi - c_lo) * TR; e += blockDim.x) {
+      const long c = c_lo + e / TR;
+      const int t = (int)(e % TR);
+      const C z = ac[c * n3 + r0 + t];
+      const long f0 = 2 * c, f1 = f0 + 1;
+      if (f0 >= f_lo) {
+        const long q = f0 - f_lo;
+        A[((q % n_occ) * SC + q / n_occ) * TR + t] = z.x;
+      }
+      if (f1 < f_hi) {
+        const long q = f1 - f_lo;
+        A[((q % n_occ) * SC + q / n_occ) * TR + t] = z.y;
+      }
     }
   }
   for (int e = tid; e < SC * TR; e += blockDim.x) {

@@ -20,10 +20,10 @@ template <typename T>
 __global__ void pair_product_kernel(int nb, const int* __restrict__ pv, const int* __restrict__ pw,
                                     const T* __restrict__ upsi, long n3, T scale,
                                     cplx<T>* __restrict__ grids) {
-  const long nc = (nb + 1) / 2;
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nc * n3) return;
-  const long c = idx / n3, r = idx - c * n3;
+  const long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long c = blockIdx.y;
+  if (r >= n3) return;
+  const long idx = c * n3 + r;
   const int p0 = (int)(2 * c), p1 = p0 + 1;
   cplx<T> F;
   F.x = upsi[pair_off<T>(pv[p0], r, n3)] * upsi[pair_off<T>(pw[p0], r, n3)] * scale;
@@ -34,29 +34,28 @@ __global__ void pair_product_kernel(int nb, const int* __restrict__ pv, const in
 template <typename T>
 cudaError_t pair_product(int nb, const int* pv, const int* pw, const T* upsi, long n3, double scale,
                          cplx<T>* grids, cudaStream_t st) {
-  const long tot = (long)((nb + 1) / 2) * n3;
-  if (!tot) return cudaSuccess;
-  pair_product_kernel<T><<<nblk(tot), 256, 0, st>>>(nb, pv, pw, upsi, n3, (T)scale, grids); note_launch();
+  if (nb <= 0) return cudaSuccess;
+  dim3 grid(nblk(n3), (nb + 1) / 2);
+  pair_product_kernel<T><<<grid, 256, 0, st>>>(nb, pv, pw, upsi, n3, (T)scale, grids); note_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
 __global__ void deinterleave_kernel(int nb, const cplx<T>* __restrict__ grids, long n3,
                                     T* __restrict__ tau) {
-  const long nc = (nb + 1) / 2;
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nc * n3) return;
-  const long c = idx / n3, r = idx - c * n3;
-  const cplx<T> F = grids[idx];
+  const long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long c = blockIdx.y;
+  if (r >= n3) return;
+  const cplx<T> F = grids[c * n3 + r];
   tau[(2 * c) * n3 + r] = F.x;
   if (2 * c + 1 < nb) tau[(2 * c + 1) * n3 + r] = F.y;
 }
 
 template <typename T>
 cudaError_t deinterleave_pairs(int nb, const cplx<T>* grids, long n3, T* tau, cudaStream_t st) {
-  const long tot = (long)((nb + 1) / 2) * n3;
-  if (!tot) return cudaSuccess;
-  deinterleave_kernel<T><<<nblk(tot), 256, 0, st>>>(nb, grids, n3, tau); note_launch();
+  if (nb <= 0) return cudaSuccess;
+  dim3 grid(nblk(n3), (nb + 1) / 2);
+  deinterleave_kernel<T><<<grid, 256, 0, st>>>(nb, grids, n3, tau); note_launch();
   return cudaGetLastError();
 }
 
@@ -288,25 +287,21 @@ __global__ void precond_diag_kernel(int n_occ, int n_pw, const T* R, const doubl
                                     const int* which, const double* g2p, const double* eps,
                                     double v0, double shift, T* out) {
   const long dim = (long)n_occ * n_pw;
-  const int t = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y, t = blockIdx.z;
+  if (j >= n_pw) return;
   const int i = which[t];
-  const double th = theta[i];
-  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < dim; e += (long)gridDim.x * blockDim.x) {
-    const int v = (int)(e / n_pw), j = (int)(e - (long)v * n_pw);
-    double den = 0.5 * g2p[j] + v0 + shift - eps[v] - th;
-    if (den < 0.1) den = 0.1;
-    out[t * dim + e] = (j == 1) ? (T)0 : (T)((double)R[(long)i * dim + e] / den);
-  }
+  double den = 0.5 * g2p[j] + v0 + shift - eps[v] - theta[i];
+  if (den < 0.1) den = 0.1;
+  const long e = (long)v * n_pw + j;
+  out[t * dim + e] = (j == 1) ? (T)0 : (T)((double)R[(long)i * dim + e] / den);
 }
 template <typename T>
 cudaError_t precond_diag(int k, int n_occ, int n_pw, const T* R, const double* theta,
                          const int* which, const double* g2p, const double* eps, double v0,
                          double shift, T* out, cudaStream_t st) {
   if (!k) return cudaSuccess;
-  const long dim = (long)n_occ * n_pw;
-  long nb = (dim + 255) / 256;
-  if (nb > 1184) nb = 1184;
-  dim3 grid((unsigned)nb, k);
+  dim3 grid(nblk(n_pw), n_occ, k);
   precond_diag_kernel<T><<<grid, 256, 0, st>>>(n_occ, n_pw, R, theta, which, g2p, eps, v0, shift, out); note_launch();
   return cudaGetLastError();
 }
@@ -385,146 +380,6 @@ cudaError_t symmetrize(int m, double* A, long lda, cudaStream_t st) {
   const long tot = (long)m * m;
   if (!tot) return cudaSuccess;
   symmetrize_kernel<<<nblk(tot), 256, 0, st>>>(m, A, lda); note_launch();
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------------
-// FP64 symmetric eigensolver for the Rayleigh-Ritz matrix: cyclic two-sided Jacobi
-// with round-robin parallel ordering (disjoint rotations applied together), one CTA.
-// A (m x m, symmetric) is read; eigenvalues ascending in w, eigenvectors as the
-// columns of V (m x m, row-major). work: m*m doubles. info: sweeps used (or -1).
-// ---------------------------------------------------------------------------------
-constexpr int JACOBI_MAX = 160;
-
-__global__ void __launch_bounds__(512) jacobi_kernel(int m, const double* __restrict__ Ain, long lda,
-                                                    double* __restrict__ Vw, double* __restrict__ V,
-                                                    double* __restrict__ w, int* info) {
-  extern __shared__ __align__(16) double jsm[];
-  const int ld = m + 1;
-  double* A = jsm;                              // m x (m+1)
-  double* cs = A + (long)m * ld;                // c[m/2+1], s[m/2+1]
-  double* sn = cs + (m / 2 + 1);
-  int* pp = reinterpret_cast<int*>(sn + (m / 2 + 1));
-  int* qq = pp + (m / 2 + 1);
-  __shared__ double red[32];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (long e = tid; e < (long)m * m; e += nt) {
-    const int i = (int)(e / m), j = (int)(e - (long)i * m);
-    A[i * ld + j] = Ain[(long)i * lda + j];
-    Vw[e] = (i == j) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  const int mp = (m + 1) & ~1;     // even number of players (index m is a bye when m is odd)
-  const int half = mp / 2;
-  // Frobenius norm for the stopping test
-  double fro = 0;
-  for (long e = tid; e < (long)m * m; e += nt) {
-    const int i = (int)(e / m), j = (int)(e - (long)i * m);
-    fro += A[i * ld + j] * A[i * ld + j];
-  }
-  fro = block_sum(fro, red);
-  __shared__ double fro_s;
-  if (tid == 0) fro_s = fro;
-  __syncthreads();
-  const double tol2 = 1e-26 * fro_s;   // stop when ||offdiag||_F <= 1e-13 ||A||_F
-  __shared__ double off_s;
-  int sweep = 0;
-  for (; sweep < 30; ++sweep) {
-    double off = 0;
-    for (long e = tid; e < (long)m * m; e += nt) {
-      const int i = (int)(e / m), j = (int)(e - (long)i * m);
-      if (i != j) off += A[i * ld + j] * A[i * ld + j];
-    }
-    __syncthreads();
-    off = block_sum(off, red);
-    if (tid == 0) off_s = off;
-    __syncthreads();
-    if (off_s <= tol2 || m < 2) break;
-    for (int rnd = 0; rnd < mp - 1; ++rnd) {
-      for (int t = tid; t < half; t += nt) {
-        int p = (t == 0) ? 0 : ((t - 1 + rnd) % (mp - 1)) + 1;
-        const int u = mp - 1 - t;
-        int q = ((u - 1 + rnd) % (mp - 1)) + 1;
-        if (p > q) { const int x = p; p = q; q = x; }
-        double c = 1.0, s = 0.0;
-        if (q < m) {
-          const double apq = A[p * ld + q];
-          if (apq != 0.0) {
-            const double tau = (A[q * ld + q] - A[p * ld + p]) / (2.0 * apq);
-            const double tt = (tau >= 0) ? 1.0 / (tau + sqrt(1.0 + tau * tau))
-                                         : -1.0 / (-tau + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + tt * tt);
-            s = tt * c;
-          }
-        }
-        pp[t] = p; qq[t] = q; cs[t] = c; sn[t] = s;
-      }
-      __syncthreads();
-      // rows: A <- J^T A
-      for (long e = tid; e < (long)half * m; e += nt) {
-        const int t = (int)(e / m), k = (int)(e - (long)t * m);
-        const int p = pp[t], q = qq[t];
-        if (q >= m || sn[t] == 0.0) continue;
-        const double c = cs[t], s = sn[t];
-        const double ap = A[p * ld + k], aq = A[q * ld + k];
-        A[p * ld + k] = c * ap - s * aq;
-        A[q * ld + k] = s * ap + c * aq;
-      }
-      __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (long e = tid; e < (long)half * m; e += nt) {
-        const int t = (int)(e / m), k = (int)(e - (long)t * m);
-        const int p = pp[t], q = qq[t];
-        if (q >= m || sn[t] == 0.0) continue;
-        const double c = cs[t], s = sn[t];
-        const double ap = A[k * ld + p], aq = A[k * ld + q];
-        A[k * ld + p] = c * ap - s * aq;
-        A[k * ld + q] = s * ap + c * aq;
-        const double vp = Vw[(long)k * m + p], vq = Vw[(long)k * m + q];
-        Vw[(long)k * m + p] = c * vp - s * vq;
-        Vw[(long)k * m + q] = s * vp + c * vq;
-      }
-      __syncthreads();
-    }
-  }
-  // sort ascending (stable by index) and permute the eigenvector columns
-  for (int i = tid; i < m; i += nt) {
-    const double di = A[i * ld + i];
-    int rank = 0;
-    for (int j = 0; j < m; ++j) {
-      const double dj = A[j * ld + j];
-      rank += (dj < di) || (dj == di && j < i);
-    }
-    w[rank] = di;
-  }
-  __syncthreads();
-  for (long e = tid; e < (long)m * m; e += nt) {
-    const int k = (int)(e / m), i = (int)(e - (long)k * m);
-    const double di = A[i * ld + i];
-    int rank = 0;
-    for (int j = 0; j < m; ++j) {
-      const double dj = A[j * ld + j];
-      rank += (dj < di) || (dj == di && j < i);
-    }
-    V[(long)k * m + rank] = Vw[e];
-  }
-  if (tid == 0) info[0] = (sweep >= 30) ? -1 : sweep;
-}
-
-cudaError_t jacobi_eigh(int m, const double* A, long lda, double* work, double* V, double* w,
-                        int* info, cudaStream_t st) {
-  if (m <= 0) return cudaSuccess;
-  if (m > JACOBI_MAX) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)m * (m + 1) * sizeof(double) + 2 * (m / 2 + 1) * sizeof(double) +
-                      2 * (m / 2 + 1) * sizeof(int) + 64;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((size_t)JACOBI_MAX * (JACOBI_MAX + 1) * 8 + 4096));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  jacobi_kernel<<<1, 512, smem, st>>>(m, A, lda, work, V, w, info); note_launch();
   return cudaGetLastError();
 }
 
