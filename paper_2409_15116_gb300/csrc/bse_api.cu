@@ -476,7 +476,7 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
   CA(al(&Tt, (size_t)b * dim)); CA(al(&Tt2, (size_t)b * dim));
   CA(al(&S1, (size_t)keep * dim)); CA(al(&S2, (size_t)keep * dim));
   CA(al(&Yt, (size_t)ms * ms)); CA(al(&Cmt, (size_t)ms * b)); CA(al(&Lt, (size_t)b * b));
-  CA(al(&Hs, (size_t)ms * ms)); CA(al(&Yv, (size_t)ms * ms)); CA(al(&jw, (size_t)ms * ms));
+  CA(al(&Hs, (size_t)ms * ms)); CA(al(&Yv, (size_t)ms * ms)); CA(al(&jw, (size_t)4 * ms * ms));
   CA(al(&theta, (size_t)ms)); CA(al(&nrm, (size_t)ms)); CA(al(&Cm, (size_t)ms * b));
   CA(al(&Sg, (size_t)b * b)); CA(al(&Linv, (size_t)b * b));
   CA(al(&info, 4)); CA(al(&which, (size_t)b));
@@ -574,17 +574,20 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
   int kk = 0;
   while (true) {
     ++it;
+    // the k lowest Ritz pairs are all the algebra needs: n_eig for the residuals and
+    // 2 n_eig for a restart; Yv is m x ky row-major
+    const int ky = std::min(m, keep);
     {
-      Scope sc(c, "davidson_eigh", 16.0 * m * m, 0.0);
-      CK(jacobi_eigh(m, Hs, ms, jw, Yv, theta, info, c->st));
+      Scope sc(c, "davidson_eigh", 8.0 * m * m, 4.0 / 3.0 * m * m * (double)m);
+      CK(eigh_lowest(m, ky, Hs, ms, jw, Yv, theta, info, c->st));
     }
     kk = std::min(ne, m);
     {
       Scope sc(c, "davidson_ritz", 2.0 * (2.0 * m + 3.0 * kk) * (double)dim * sizeof(T),
                4.0 * kk * m * (double)dim);
-      CK((convert<double, T>((long)m * m, Yv, Yt, c->st)));
-      CK((gemm<T, T>(true, false, kk, (int)dim, m, 1.0, Yt, m, V, dim, 0.0, X, dim, 1, c->st)));
-      CK((gemm<T, T>(true, false, kk, (int)dim, m, 1.0, Yt, m, W, dim, 0.0, LX, dim, 1, c->st)));
+      CK((convert<double, T>((long)m * ky, Yv, Yt, c->st)));
+      CK((gemm<T, T>(true, false, kk, (int)dim, m, 1.0, Yt, ky, V, dim, 0.0, X, dim, 1, c->st)));
+      CK((gemm<T, T>(true, false, kk, (int)dim, m, 1.0, Yt, ky, W, dim, 0.0, LX, dim, 1, c->st)));
       CK(residuals<T>(kk, dim, X, LX, theta, Rr, nrm, c->st));
     }
     CK(cudaMemcpyAsync(th.data(), theta, sizeof(double) * kk, cudaMemcpyDeviceToHost, c->st));
@@ -610,8 +613,8 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
     }
     if (m + nt > ms) {
       const int kp = std::min(keep, m);
-      CK((gemm<T, T>(true, false, kp, (int)dim, m, 1.0, Yt, m, V, dim, 0.0, S1, dim, 1, c->st)));
-      CK((gemm<T, T>(true, false, kp, (int)dim, m, 1.0, Yt, m, W, dim, 0.0, S2, dim, 1, c->st)));
+      CK((gemm<T, T>(true, false, kp, (int)dim, m, 1.0, Yt, ky, V, dim, 0.0, S1, dim, 1, c->st)));
+      CK((gemm<T, T>(true, false, kp, (int)dim, m, 1.0, Yt, ky, W, dim, 0.0, S2, dim, 1, c->st)));
       CK(cudaMemcpyAsync(V, S1, sizeof(T) * kp * dim, cudaMemcpyDeviceToDevice, c->st));
       CK(cudaMemcpyAsync(W, S2, sizeof(T) * kp * dim, cudaMemcpyDeviceToDevice, c->st));
       m = kp;

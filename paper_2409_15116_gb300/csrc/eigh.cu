@@ -1,126 +1,254 @@
-// FP64 symmetric eigensolver for the Davidson Rayleigh-Ritz matrix (m <= 160), one CTA.
+// FP64 symmetric eigensolver for the Davidson Rayleigh-Ritz matrix (m <= 160), one CTA,
+// returning the k lowest eigenpairs.
 //
-// One-sided (Hestenes) Jacobi on G = A + s I, with the shift s taken from Gershgorin's
-// lower bound so that G is positive definite: plane rotations orthogonalise the columns
-// of G in place, V accumulates them, and at convergence the columns of V are the
-// eigenvectors of A. Each warp owns disjoint column pairs of a round-robin round (its
-// three dot products are warp-shuffle reductions), so a round needs a single CTA-wide
-// barrier. Eigenvalues are recomputed as v_i^T (A + s I) v_i - s, i.e. v_i . g_i - s.
+//  1. Householder tridiagonalisation T = Q^T A Q in shared memory (reflector vectors kept
+//     in the strictly lower part of A).
+//  2. Each of the k lowest eigenvalues of T by bisection on the Sturm count of the
+//     LDL^T recurrence (one thread per eigenvalue).
+//  3. Eigenvectors of T by inverse iteration (tridiagonal elimination with partial
+//     pivoting), re-orthogonalised against earlier members of the same cluster.
+//  4. Back-transformation v = Q z with the stored reflectors.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace bse {
 
 constexpr int EIGH_MAX = 160;
+constexpr int EIGH_KMAX = 64;
 
-__device__ __forceinline__ double warp_sum(double v) {
+__device__ __forceinline__ double blk_sum(double v, double* sh) {
+  __syncthreads();
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+  return t;
 }
 
-__global__ void __launch_bounds__(512) hestenes_kernel(int m, const double* __restrict__ A, long lda,
-                                                      double* __restrict__ Vc, double* __restrict__ Vout,
-                                                      double* __restrict__ w, int* info) {
-  extern __shared__ __align__(16) double G[];   // column-major, G[j*m + i] = G(i, j)
+// Sturm count: number of eigenvalues of T (diag d, off-diagonal e) strictly below x
+__device__ int sturm_count(int m, const double* d, const double* e2, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0) ++cnt;
+  for (int i = 1; i < m; ++i) {
+    q = d[i] - x - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void __launch_bounds__(512) eigh_lowest_kernel(int m, int k, const double* __restrict__ Ain,
+                                                         long lda, double* __restrict__ Z,
+                                                         double* __restrict__ S, double* __restrict__ V,
+                                                         double* __restrict__ w, int* info) {
+  extern __shared__ __align__(16) double sm[];
+  const int ld = m + 1;
+  double* A = sm;                    // m x (m+1)
+  double* d = A + (long)m * ld;      // m
+  double* e = d + m;                 // m
+  double* e2 = e + m;                // m
+  double* p = e2 + m;                // m
+  double* lam = p + m;               // EIGH_KMAX
   __shared__ double red[32];
-  __shared__ double shift_s;
-  __shared__ int rot_count;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  // Gershgorin lower bound of the spectrum
-  double lo = 1e300;
-  for (int i = tid; i < m; i += blockDim.x) {
-    double off = 0;
-    for (int j = 0; j < m; ++j)
-      if (j != i) off += fabs(A[(long)i * lda + j]);
-    lo = fmin(lo, A[(long)i * lda + i] - off);
-  }
-  for (int o = 16; o > 0; o >>= 1) lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-  if (lane == 0) red[warp] = lo;
-  __syncthreads();
-  if (tid == 0) {
-    double l = red[0];
-    for (int i = 1; i < nwarps; ++i) l = fmin(l, red[i]);
-    shift_s = (l < 0 ? -l : 0.0) + 0.25 * (fabs(l) + 1e-3);
+  __shared__ double s_alpha, s_scale;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (long x = tid; x < (long)m * m; x += nt) {
+    const int i = (int)(x / m), j = (int)(x - (long)i * m);
+    A[i * ld + j] = Ain[(long)i * lda + j];
   }
   __syncthreads();
-  const double s0 = shift_s;
-  for (long e = tid; e < (long)m * m; e += blockDim.x) {
-    const int j = (int)(e / m), i = (int)(e - (long)j * m);
-    G[e] = A[(long)i * lda + j] + (i == j ? s0 : 0.0);
-    Vc[e] = (i == j) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  const int mp = (m + 1) & ~1, half = mp / 2;
-  int sweep = 0;
-  for (; sweep < 40 && m > 1; ++sweep) {
-    if (tid == 0) rot_count = 0;
+  // ---- 1. tridiagonalisation ----
+  for (int c = 0; c + 2 < m; ++c) {
+    const int n = m - c - 1;                      // length of the column below the diagonal
+    double s2 = 0;
+    for (int i = tid; i < n; i += nt) { const double x = A[(c + 1 + i) * ld + c]; s2 += x * x; }
+    s2 = blk_sum(s2, red);
+    if (tid == 0) {
+      const double x0 = A[(c + 1) * ld + c];
+      const double nrm = sqrt(s2);
+      const double alpha = (x0 >= 0) ? -nrm : nrm;
+      d[c] = A[c * ld + c];
+      e[c] = (nrm == 0.0) ? 0.0 : alpha;
+      // v = x - alpha e1, |v|^2 = s2 - 2 alpha x0 + alpha^2
+      const double vn2 = s2 - 2.0 * alpha * x0 + alpha * alpha;
+      s_alpha = alpha;
+      s_scale = (nrm == 0.0 || vn2 <= 0.0) ? 0.0 : 1.0 / sqrt(vn2);
+    }
     __syncthreads();
-    for (int rnd = 0; rnd < mp - 1; ++rnd) {
-      for (int t = warp; t < half; t += nwarps) {
-        int p = (t == 0) ? 0 : ((t - 1 + rnd) % (mp - 1)) + 1;
-        int q = ((mp - 2 - t + rnd) % (mp - 1)) + 1;
-        if (p > q) { const int x = p; p = q; q = x; }
-        if (q >= m) continue;
-        double* gp = G + (long)p * m;
-        double* gq = G + (long)q * m;
-        double a = 0, b = 0, g = 0;
-        for (int i = lane; i < m; i += 32) {
-          const double x = gp[i], y = gq[i];
-          a += x * x; b += y * y; g += x * y;
+    const double sc = s_scale;
+    // u = v / |v| stored in place of the column (zero reflector if sc == 0)
+    for (int i = tid; i < n; i += nt) {
+      const double x = A[(c + 1 + i) * ld + c];
+      A[(c + 1 + i) * ld + c] = (i == 0 ? x - s_alpha : x) * sc;
+    }
+    __syncthreads();
+    if (sc == 0.0) continue;
+    // p = B u over the trailing block B = A[c+1:, c+1:] (symmetric, both halves valid)
+    for (int i = tid; i < n; i += nt) {
+      double acc = 0;
+      const double* row = A + (c + 1 + i) * ld + (c + 1);
+      for (int j = 0; j < n; ++j) acc += row[j] * A[(c + 1 + j) * ld + c];
+      p[i] = acc;
+    }
+    double kk = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) kk += A[(c + 1 + i) * ld + c] * p[i];
+    kk = blk_sum(kk, red);
+    // q = p - K u (kept in p), B -= 2 (u q^T + q u^T)
+    for (int i = tid; i < n; i += nt) p[i] -= kk * A[(c + 1 + i) * ld + c];
+    __syncthreads();
+    for (int x = tid; x < n * n; x += nt) {
+      const int i = x / n, j = x - i * n;
+      const double ui = A[(c + 1 + i) * ld + c], uj = A[(c + 1 + j) * ld + c];
+      A[(c + 1 + i) * ld + (c + 1 + j)] -= 2.0 * (ui * p[j] + p[i] * uj);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (m >= 2) {
+      d[m - 2] = A[(m - 2) * ld + (m - 2)];
+      e[m - 2] = A[(m - 1) * ld + (m - 2)];
+    }
+    d[m - 1] = A[(m - 1) * ld + (m - 1)];
+    e[m - 1] = 0.0;
+  }
+  __syncthreads();
+  for (int i = tid; i < m; i += nt) e2[i] = e[i] * e[i];
+  __syncthreads();
+  // ---- 2. bisection for the k lowest eigenvalues ----
+  double gl = 1e300, gu = -1e300, tnorm = 0;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
+    gl = fmin(gl, d[i] - r);
+    gu = fmax(gu, d[i] + r);
+  }
+  tnorm = fmax(fabs(gl), fabs(gu));
+  const double pivmin = 1e-290 + 1e-300 * tnorm * tnorm;
+  for (int j = tid; j < k; j += nt) {
+    double lo = gl - 1e-14 * tnorm - 1e-300, hi = gu + 1e-14 * tnorm + 1e-300;
+    for (int it = 0; it < 200 && hi - lo > 2.2e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (sturm_count(m, d, e2, mid, pivmin) > j) hi = mid; else lo = mid;
+    }
+    lam[j] = 0.5 * (lo + hi);
+  }
+  __syncthreads();
+  // ---- 3. inverse iteration, one thread per eigenvector (Z column-major, m x k) ----
+  const double ortol = 1e-3 * tnorm;
+  for (int j = tid; j < k; j += nt) {
+    double* z = Z + (long)j * m;
+    // perturb the shift slightly inside clusters so the factorisation stays regular
+    double mu = lam[j];
+    for (int i = 0; i < j; ++i)
+      if (fabs(lam[i] - mu) < 1e-14 * tnorm) mu = lam[i] + 1e-14 * tnorm * (j - i);
+    for (int i = 0; i < m; ++i) z[i] = 1.0 / sqrt((double)m) * (1.0 + 0.001 * ((i * 7 + j * 13) % 11));
+    for (int pass = 0; pass < 3; ++pass) {
+      // solve (T - mu I) y = z by elimination with partial pivoting; the upper factor has
+      // up to two super-diagonals (u0 diag, u1, u2); y overwrites z
+      double* u0 = S + (long)j * 3 * m;
+      double* u1 = u0 + m;
+      double* u2 = u1 + m;
+      double a0 = d[0] - mu, b0 = (m > 1) ? e[0] : 0.0, c0 = 0.0;
+      double rhs = z[0];
+      for (int i = 0; i + 1 < m; ++i) {
+        const double sub = e[i];
+        const double a1 = d[i + 1] - mu, b1 = (i + 2 < m) ? e[i + 1] : 0.0;
+        double r1 = z[i + 1];
+        if (fabs(sub) > fabs(a0)) {          // swap rows i and i+1
+          const double f = a0 / sub;
+          u0[i] = sub; u1[i] = a1; u2[i] = b1;
+          z[i] = r1;
+          const double na0 = b0 - f * a1, nb0 = c0 - f * b1;
+          r1 = rhs - f * r1;
+          a0 = na0; b0 = nb0; c0 = 0.0; rhs = r1;
+        } else {
+          if (a0 == 0.0) a0 = pivmin;
+          const double f = sub / a0;
+          u0[i] = a0; u1[i] = b0; u2[i] = c0;
+          z[i] = rhs;
+          a0 = a1 - f * b0; b0 = b1 - f * c0; c0 = 0.0; rhs = r1 - f * rhs;
         }
-        a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
-        if (g == 0.0 || fabs(g) <= 1e-15 * sqrt(a * b)) continue;
-        const double zeta = (b - a) / (2.0 * g);
-        const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
-        double* vp = Vc + (long)p * m;
-        double* vq = Vc + (long)q * m;
-        for (int i = lane; i < m; i += 32) {
-          const double x = gp[i], y = gq[i];
-          gp[i] = c * x - s * y; gq[i] = s * x + c * y;
-          const double u = vp[i], z = vq[i];
-          vp[i] = c * u - s * z; vq[i] = s * u + c * z;
-        }
-        if (lane == 0) atomicAdd(&rot_count, 1);
       }
+      if (a0 == 0.0) a0 = pivmin;
+      u0[m - 1] = a0;
+      z[m - 1] = rhs;
+      // back substitution
+      for (int i = m - 1; i >= 0; --i) {
+        double s = z[i];
+        if (i + 1 < m) s -= u1[i] * z[i + 1];
+        if (i + 2 < m) s -= u2[i] * z[i + 2];
+        z[i] = s / u0[i];
+      }
+      double nn = 0;
+      for (int i = 0; i < m; ++i) nn += z[i] * z[i];
+      nn = 1.0 / sqrt(nn);
+      for (int i = 0; i < m; ++i) z[i] *= nn;
+    }
+  }
+  __syncthreads();
+  // re-orthogonalise inside clusters (modified Gram-Schmidt in eigenvalue order)
+  for (int j = 1; j < k; ++j) {
+    for (int i = 0; i < j; ++i) {
+      if (fabs(lam[j] - lam[i]) > ortol) continue;
+      double dot = 0;
+      for (int r = tid; r < m; r += nt) dot += Z[(long)i * m + r] * Z[(long)j * m + r];
+      dot = blk_sum(dot, red);
+      for (int r = tid; r < m; r += nt) Z[(long)j * m + r] -= dot * Z[(long)i * m + r];
       __syncthreads();
     }
-    if (rot_count == 0) break;
+    double nn = 0;
+    for (int r = tid; r < m; r += nt) nn += Z[(long)j * m + r] * Z[(long)j * m + r];
+    nn = blk_sum(nn, red);
+    const double inv = 1.0 / sqrt(nn);
+    for (int r = tid; r < m; r += nt) Z[(long)j * m + r] *= inv;
     __syncthreads();
   }
-  // eigenvalues: theta_i = v_i . g_i - s (g_i = (A + sI) v_i)
-  __shared__ double th[EIGH_MAX];
-  for (int i = warp; i < m; i += nwarps) {
-    double d = 0;
-    for (int k = lane; k < m; k += 32) d += Vc[(long)i * m + k] * G[(long)i * m + k];
-    d = warp_sum(d);
-    if (lane == 0) th[i] = d - s0;
+  // ---- 4. back-transformation: v = H_0 H_1 ... H_{m-3} z, applied to all k vectors ----
+  for (int c = m - 3; c >= 0; --c) {
+    const int n = m - c - 1;
+    // one warp per vector: dot = u . z[c+1:], z[c+1:] -= 2 dot u
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    for (int j = wid; j < k; j += nw) {
+      double* z = Z + (long)j * m;
+      double dot = 0;
+      for (int i = lane; i < n; i += 32) dot += A[(c + 1 + i) * ld + c] * z[c + 1 + i];
+      for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+      for (int i = lane; i < n; i += 32) z[c + 1 + i] -= 2.0 * dot * A[(c + 1 + i) * ld + c];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (long e = tid; e < (long)m * m; e += blockDim.x) {
-    const int i = (int)(e / m), k = (int)(e - (long)i * m);   // column i, row k
-    const double di = th[i];
-    int rank = 0;
-    for (int j = 0; j < m; ++j) rank += (th[j] < di) || (th[j] == di && j < i);
-    Vout[(long)k * m + rank] = Vc[e];
-    if (k == 0) w[rank] = di;
+  // outputs: V row-major m x k (component r of eigenvector j at V[r*k + j]), w[0..k)
+  for (long x = tid; x < (long)m * k; x += nt) {
+    const int r = (int)(x / k), j = (int)(x - (long)r * k);
+    V[x] = Z[(long)j * m + r];
   }
-  if (tid == 0) info[0] = (sweep >= 40) ? -1 : sweep;
+  for (int j = tid; j < k; j += nt) w[j] = lam[j];
+  if (tid == 0) info[0] = 0;
 }
 
-cudaError_t jacobi_eigh(int m, const double* A, long lda, double* work, double* V, double* w,
+// k lowest eigenpairs of the symmetric m x m matrix A (lda): eigenvalues ascending in w[0..k),
+// eigenvectors as the columns of V (row-major m x k). work: at least 4*m*k doubles.
+cudaError_t eigh_lowest(int m, int k, const double* A, long lda, double* work, double* V, double* w,
                         int* info, cudaStream_t st) {
-  if (m <= 0) return cudaSuccess;
-  if (m > EIGH_MAX) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)m * m * sizeof(double);
+  if (m <= 0 || k <= 0) return cudaSuccess;
+  if (m > EIGH_MAX || k > EIGH_KMAX || k > m) return cudaErrorInvalidValue;
+  const size_t smem = ((size_t)m * (m + 1) + 4 * (size_t)m + EIGH_KMAX) * sizeof(double);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(hestenes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((size_t)EIGH_MAX * EIGH_MAX * sizeof(double)));
+    const size_t mx = ((size_t)EIGH_MAX * (EIGH_MAX + 1) + 4 * EIGH_MAX + EIGH_KMAX) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(eigh_lowest_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  hestenes_kernel<<<1, 512, smem, st>>>(m, A, lda, work, V, w, info);
+  double* Z = work;                       // m x k, column-major
+  double* scratch = work + (size_t)m * k; // 3 m per vector
+  eigh_lowest_kernel<<<1, 512, smem, st>>>(m, k, A, lda, Z, scratch, V, w, info);
   note_launch();
   return cudaGetLastError();
 }

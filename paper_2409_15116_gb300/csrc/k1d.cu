@@ -83,27 +83,36 @@ __global__ void __launch_bounds__(256) k1d_tile_kernel(
 #pragma unroll
       for (int s = 0; s < SC; ++s) acc[i][s] = (T)0;
     const int e0 = bptr[rb], e1 = bptr[rb + 1];
-    // one-deep software pipeline on the tau loads
-    int wn = 0;
-    T tn0 = 0, tn1 = 0, tn2 = 0, tn3 = 0;
-    if (e0 < e1) {
-      const int4 p = bp[e0];
-      wn = bw[e0];
-      tn0 = p.x >= 0 ? tau[(long)p.x * n3 + r] : (T)0;
-      tn1 = p.y >= 0 ? tau[(long)p.y * n3 + r] : (T)0;
-      tn2 = p.z >= 0 ? tau[(long)p.z * n3 + r] : (T)0;
-      tn3 = p.w >= 0 ? tau[(long)p.w * n3 + r] : (T)0;
+    // two-deep software pipeline on the tau loads (entries e+1 and e+2 in flight)
+    T tq[2][4];
+    int wq[2];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const int e = e0 + d;
+      wq[d] = 0;
+      tq[d][0] = tq[d][1] = tq[d][2] = tq[d][3] = (T)0;
+      if (e < e1) {
+        const int4 p = bp[e];
+        wq[d] = bw[e];
+        tq[d][0] = p.x >= 0 ? tau[(long)p.x * n3 + r] : (T)0;
+        tq[d][1] = p.y >= 0 ? tau[(long)p.y * n3 + r] : (T)0;
+        tq[d][2] = p.z >= 0 ? tau[(long)p.z * n3 + r] : (T)0;
+        tq[d][3] = p.w >= 0 ? tau[(long)p.w * n3 + r] : (T)0;
+      }
     }
     for (int e = e0; e < e1; ++e) {
-      const int w = wn;
-      const T t0 = tn0, t1 = tn1, t2 = tn2, t3 = tn3;
-      if (e + 1 < e1) {
-        const int4 p = bp[e + 1];
-        wn = bw[e + 1];
-        tn0 = p.x >= 0 ? tau[(long)p.x * n3 + r] : (T)0;
-        tn1 = p.y >= 0 ? tau[(long)p.y * n3 + r] : (T)0;
-        tn2 = p.z >= 0 ? tau[(long)p.z * n3 + r] : (T)0;
-        tn3 = p.w >= 0 ? tau[(long)p.w * n3 + r] : (T)0;
+      const int w = wq[0];
+      const T t0 = tq[0][0], t1 = tq[0][1], t2 = tq[0][2], t3 = tq[0][3];
+      wq[0] = wq[1];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) tq[0][i] = tq[1][i];
+      if (e + 2 < e1) {
+        const int4 p = bp[e + 2];
+        wq[1] = bw[e + 2];
+        tq[1][0] = p.x >= 0 ? tau[(long)p.x * n3 + r] : (T)0;
+        tq[1][1] = p.y >= 0 ? tau[(long)p.y * n3 + r] : (T)0;
+        tq[1][2] = p.z >= 0 ? tau[(long)p.z * n3 + r] : (T)0;
+        tq[1][3] = p.w >= 0 ? tau[(long)p.w * n3 + r] : (T)0;
       }
       const T* Aw = A + (size_t)w * SC * TR + t;
 #pragma unroll
@@ -153,8 +162,12 @@ static cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T
 }
 
 // shared-memory budget of the a(r) stage; SC (vectors per CTA) is the largest power of
-// two with n_occ * SC * TR * sizeof(T) within it
-constexpr size_t K1D_SMEM_BUDGET = 160 * 1024;
+// two with n_occ * SC * TR * sizeof(T) within it. A budget near 72 KB lets three CTAs
+// (24 warps) share an SM, which the tau loads need for latency hiding.
+#ifndef BSE_K1D_SMEM_KB
+#define BSE_K1D_SMEM_KB 72
+#endif
+constexpr size_t K1D_SMEM_BUDGET = (size_t)BSE_K1D_SMEM_KB * 1024;
 
 template <typename T>
 int k1d_vectors_per_cta(int n_occ) {

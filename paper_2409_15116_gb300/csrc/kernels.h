@@ -75,7 +75,7 @@ template <typename T>
 cudaError_t set_unit(T* x, long dim, long idx, cudaStream_t st);
 cudaError_t symmetrize(int m, double* A, long lda, cudaStream_t st);
 cudaError_t mirror_new(double* A, long lda, int m0, int m1, cudaStream_t st);
-cudaError_t jacobi_eigh(int m, const double* A, long lda, double* work, double* V, double* w,
+cudaError_t eigh_lowest(int m, int k, const double* A, long lda, double* work, double* V, double* w,
                         int* info, cudaStream_t st);
 cudaError_t cholesky_inverse(int b, const double* S, long lds, double* Linv, int* info,
                              cudaStream_t st);
