@@ -291,7 +291,7 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
       Scope sc(c, "k1d_combine",
                ((double)c->n_pairs + 2.0 * nf + 1.0 + nv + c->n_occ) * n3 * sz,
                (2.0 * nnz * nv + 5.0 * nf) * n3);
-      if (k1d_vectors_per_cta<T>(c->n_occ) > 0 && n3 % 16 == 0) {
+      if (k1d_vectors_per_cta<T>(c->n_occ) > 0 && n3 % 32 == 0) {
         CK(k1d_tiled<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->bptr, c->bw, c->bp,
                         c->n_rblocks, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
       } else {

@@ -169,9 +169,13 @@ static cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T
 #endif
 constexpr size_t K1D_SMEM_BUDGET = (size_t)BSE_K1D_SMEM_KB * 1024;
 
+#ifndef BSE_K1D_TR
+#define BSE_K1D_TR 16
+#endif
+
 template <typename T>
 int k1d_vectors_per_cta(int n_occ) {
-  constexpr int TR = 16;
+  constexpr int TR = BSE_K1D_TR;
   for (int sc = 8; sc >= 1; sc >>= 1)
     if ((size_t)n_occ * sc * TR * sizeof(T) + sc * TR * sizeof(T) <= K1D_SMEM_BUDGET) return sc;
   return 0;
@@ -181,7 +185,7 @@ template <typename T>
 cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, const int* bptr,
                       const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
                       const T* upsi, double sf, T* out, cudaStream_t st) {
-  constexpr int TR = 16;
+  constexpr int TR = BSE_K1D_TR;
   if (n_vec <= 0) return cudaSuccess;
   if (n3 % TR) return cudaErrorInvalidValue;
   switch (k1d_vectors_per_cta<T>(n_occ)) {
