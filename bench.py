@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
+    ap.add_argument("--apply-only", action="store_true",
+                    help="time bse_apply_liouville alone on --nvec vectors (operator GB/s)")
+    ap.add_argument("--nvec", type=int, default=32)
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     return ap.parse_args()
 
@@ -151,6 +154,40 @@ def cpu_oracle_sample(inst, n_apply_vectors: int, budget_s: float):
 
 
 # --------------------------------------------------------------------------------------
+def apply_only(args, inst, ctx, stream, binding):
+    """Operator-only timing: one bse_apply_liouville on a block of random conduction vectors."""
+    import numpy as np
+    import torch
+    ctx.build_tau()
+    rng = np.random.default_rng(0)
+    psi = inst.psi
+    A = rng.standard_normal((args.nvec, inst.n_occ, inst.n_pw))
+    A -= (A @ psi.T) @ psi
+    A[..., 1] = 0.0
+    a = torch.tensor(A, dtype=torch.float32, device="cuda")
+    out = torch.empty_like(a)
+    for _ in range(args.warmup):
+        ctx.apply(a, out)
+    torch.cuda.synchronize()
+    ctx.profile(-1)
+    ctx.profile(1)
+    l0 = binding.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.apply(a, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.profile(0)
+    prof, nl = ctx.profile_read()
+    ms = e0.elapsed_time(e1) / args.steps
+    regions = {k: {"ms": v["ms"] / v["calls"], "GBps": v["bytes"] / (v["ms"] * 1e-3) / 1e9,
+                   "TFLOPs": v["flops"] / (v["ms"] * 1e-3) / 1e12}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+    print(json.dumps({"mode": "apply_only", "config": args.config, "nvec": args.nvec,
+                      "ms_per_apply": ms, "gpu_launches": nl - l0, "regions": regions}), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -206,6 +243,9 @@ def main():
     def step():
         ctx.build_tau()
         return ctx.davidson(N_EIG, BLOCK, MAX_SUB, max_it=200, res_tol=TOL_MIXED)
+
+    if args.apply_only:
+        return apply_only(args, inst, ctx, stream, binding)
 
     for _ in range(args.warmup):
         om_mixed, st = step()

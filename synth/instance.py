@@ -338,6 +338,9 @@ CONFIGS = {
     # small profiling case of the same family: 48^3, 64 orbitals, 128 PDEP (~1 GB of fields)
     "small": lambda s=None: make_localized(8 if s is None else s, 20.0 * 48 / 72, 48, 64, 2.5, 128,
                                            name="small-L13.3-N48-occ64"),
+    # operator profiling case with the medium orbital count on a 32^3 grid (~3 GB of fields)
+    "op256": lambda s=None: make_localized(9 if s is None else s, 20.0 * 32 / 72, 32, 256, 2.5, 512,
+                                           name="op256-L8.9-N32-occ256"),
     # one member of the uneven batch (seeds 300..363)
     "batch": lambda s=None: make_batched_member(300 if s is None else s),
     # large: 96^3, 1024 orbitals, 1024 PDEP, ~20k pairs
