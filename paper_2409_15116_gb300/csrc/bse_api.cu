@@ -56,8 +56,24 @@ struct Prof {
   }
 };
 
+// opaque storage for a TMA tensor map (CUtensorMap is 128 bytes, 64-byte aligned)
+struct TMap { alignas(64) unsigned char b[128]; };
+// bf16 hi/lo split of an operand with its two tensor maps
+struct Split {
+  void* hi = nullptr;
+  void* lo = nullptr;
+  long rows = 0, cols = 0, ld = 0;
+  TMap mhi, mlo;
+};
+
 struct bse_ctx {
   Prof prof;
+  // tensor-core (BF16x3) operands of the mixed path
+  bool tc_ok = false;
+  Split psi_s, psiT_s, pdep_s, pdepT_s;
+  void *ws_ahi = nullptr, *ws_alo = nullptr, *ws_bhi = nullptr, *ws_blo = nullptr;
+  long ws_split_rows = 0;
+  int* d_err = nullptr;
   // problem
   int N = 0;
   long n3 = 0;
@@ -158,6 +174,60 @@ inline double fft_flops(long n3, long grids) { return 5.0 * (double)n3 * std::lo
 
 bool all_finite(const double* x, long n) { return finite_check_host(x, n); }
 
+inline long pad8(long x) { return (x + 7) / 8 * 8; }
+
+// split a resident FP64 matrix [rows x cols] (optionally transposed) into bf16 hi/lo with maps
+int make_split64(bse_ctx* c, Split& sp, const double* X, long rows, long cols, bool transpose) {
+  sp.rows = transpose ? cols : rows;
+  sp.cols = transpose ? rows : cols;
+  sp.ld = pad8(sp.cols);
+  unsigned short *h, *l;
+  CA(dalloc(c, &h, (size_t)sp.rows * sp.ld));
+  CA(dalloc(c, &l, (size_t)sp.rows * sp.ld));
+  sp.hi = h; sp.lo = l;
+  CK(bf16_split64(X, rows, (int)cols, cols, h, l, sp.ld, transpose, c->st));
+  // maps span the zero-padded width so the inner extent is at least 16 bytes
+  if (!tc_make_map(sp.mhi.b, sp.hi, sp.rows, sp.ld, sp.ld) || !tc_make_map(sp.mlo.b, sp.lo, sp.rows, sp.ld, sp.ld))
+    return fail(c, BSE_ERR_CUDA, "TMA tensor map creation failed");
+  return BSE_OK;
+}
+
+// workspace for the per-call splits: A operand (K = n_pw) and the small-K operand
+int ensure_split_ws(bse_ctx* c, long rows) {
+  if (rows <= c->ws_split_rows) return BSE_OK;
+  dfree(c, c->ws_ahi); dfree(c, c->ws_alo); dfree(c, c->ws_bhi); dfree(c, c->ws_blo);
+  c->ws_ahi = c->ws_alo = c->ws_bhi = c->ws_blo = nullptr;
+  c->ws_split_rows = 0;
+  const long ldk = pad8(c->n_pw), lds = pad8(std::max(c->n_occ, std::max(1, c->n_pdep)));
+  unsigned short* p;
+  CA(dalloc(c, &p, (size_t)rows * ldk)); c->ws_ahi = p;
+  CA(dalloc(c, &p, (size_t)rows * ldk)); c->ws_alo = p;
+  CA(dalloc(c, &p, (size_t)rows * lds)); c->ws_bhi = p;
+  CA(dalloc(c, &p, (size_t)rows * lds)); c->ws_blo = p;
+  c->ws_split_rows = rows;
+  return BSE_OK;
+}
+
+// out[M x N] = alpha * X[M x K] * B^T + beta * out  with B given by a resident split (N x K)
+int tc_product(bse_ctx* c, const float* X, long M, long K, long ldx, const Split& B, bool small_k_slot,
+               float* out, long ldo, double alpha, double beta) {
+  CA(ensure_split_ws(c, M));
+  const long ld = pad8(K);
+  void* hi = small_k_slot ? c->ws_bhi : c->ws_ahi;
+  void* lo = small_k_slot ? c->ws_blo : c->ws_alo;
+  CK(bf16_split(X, M, (int)K, ldx, hi, lo, ld, c->st));
+  TMap mh, ml;
+  if (!tc_make_map(mh.b, hi, M, ld, ld) || !tc_make_map(ml.b, lo, M, ld, ld))
+    return fail(c, BSE_ERR_CUDA, "TMA tensor map creation failed");
+  const long tiles = ((M + 127) / 128) * ((B.rows + 127) / 128);
+  const long kt = (K + 63) / 64;
+  int splits = 1;
+  if (beta == 0.0 && tiles < 2 * 152) splits = (int)std::min<long>(std::max<long>(1, 304 / tiles), std::max<long>(1, kt / 4));
+  CK(tc_gemm_bf16x3(mh.b, ml.b, B.mhi.b, B.mlo.b, (int)M, (int)B.rows, (int)K, alpha, beta, out, ldo,
+                    splits, c->d_err, c->st));
+  return BSE_OK;
+}
+
 // threshold rule of the pair list (same reading as documented in bse.h)
 double choose_threshold(const std::vector<double>& O, int n, double thr, int64_t keep) {
   if (thr > 0) return thr;
@@ -206,6 +276,15 @@ template <> const float2* tw_of<float>(bse_ctx* c) { return c->tw32; }
 template <typename T>
 int project(bse_ctx* c, long rows, T* X, T* cbuf) {
   if (rows <= 0) return BSE_OK;
+  if constexpr (sizeof(T) == 4) {
+    if (c->tc_ok) {
+      // C = X Psi^T (BF16x3 tensor cores), X -= C Psi
+      CA(tc_product(c, (const float*)X, rows, c->n_pw, c->n_pw, c->psi_s, false, (float*)cbuf, c->n_occ, 1.0, 0.0));
+      CA(tc_product(c, (const float*)cbuf, rows, c->n_occ, c->n_occ, c->psiT_s, true, (float*)X, c->n_pw, -1.0, 1.0));
+      CK(zero_pad_column<T>((int)rows, c->n_pw, X, c->st));
+      return BSE_OK;
+    }
+  }
   const T* psi = psi_of<T>(c);
   // cbuf [rows x n_occ] = X psi^T ; X -= cbuf psi
   CK((gemm<T, T>(false, true, (int)rows, c->n_occ, c->n_pw, 1.0, X, c->n_pw, psi, c->n_pw, 0.0,
@@ -424,11 +503,22 @@ int build_tau_impl(bse_ctx* c) {
     if (c->n_pdep > 0) {
       CK((sphere_pack<T, T>(grids, b, c->n_pw, c->n_half, c->gpos, c->gneg, n3, 1.0, X, nullptr,
                             nullptr, nullptr, 0.0, 1, c->st)));
-      CK((gemm<T, T>(false, true, b, c->n_pdep, c->n_pw, 1.0, X, c->n_pw, pd, c->n_pw, 0.0, Cp,
-                     c->n_pdep, 1, c->st)));
-      CK(scale_columns<T>(b, c->n_pdep, Cp, c->n_pdep, c->f, c->st));
-      CK((gemm<T, T>(false, false, b, c->n_pw, c->n_pdep, 1.0, Cp, c->n_pdep, pd, c->n_pw, 0.0, X2,
-                     c->n_pw, 1, c->st)));
+      bool done = false;
+      if constexpr (sizeof(T) == 4) {
+        if (c->tc_ok) {
+          CA(tc_product(c, (const float*)X, b, c->n_pw, c->n_pw, c->pdep_s, false, (float*)Cp, c->n_pdep, 1.0, 0.0));
+          CK(scale_columns<T>(b, c->n_pdep, Cp, c->n_pdep, c->f, c->st));
+          CA(tc_product(c, (const float*)Cp, b, c->n_pdep, c->n_pdep, c->pdepT_s, true, (float*)X2, c->n_pw, 1.0, 0.0));
+          done = true;
+        }
+      }
+      if (!done) {
+        CK((gemm<T, T>(false, true, b, c->n_pdep, c->n_pw, 1.0, X, c->n_pw, pd, c->n_pw, 0.0, Cp,
+                       c->n_pdep, 1, c->st)));
+        CK(scale_columns<T>(b, c->n_pdep, Cp, c->n_pdep, c->f, c->st));
+        CK((gemm<T, T>(false, false, b, c->n_pw, c->n_pdep, 1.0, Cp, c->n_pdep, pd, c->n_pw, 0.0, X2,
+                       c->n_pw, 1, c->st)));
+      }
       CK((sphere_unpack<T, T>(X2, b, c->n_pw, c->n_half, c->gpos, c->gneg, grids, n3, false, true, c->st)));
     }
     CK(grid_coulomb<T>(grids, ng, c->N, c->L, c->omega, 1, 1.0, c->st));
@@ -838,11 +928,33 @@ int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) 
         e = convert<double, float>((long)c->n_pdep * c->n_pw, c->pdep64, c->pdep32, c->st);
       }
       if (e != cudaSuccess) return bail(cuda_fail(c, e, "FP32 copies"));
+      // BF16x3 tensor-core operands: Psi, Psi^T, Phi, Phi^T split once
+      if ((r = dalloc(c, &c->d_err, 1)) != BSE_OK) return bail(r);
+      if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st)) != cudaSuccess) return bail(cuda_fail(c, e, "err flag"));
+      if (tc_map_bytes() == sizeof(TMap) && getenv("BSE_NO_TENSOR_CORES") == nullptr) {
+        int rr = make_split64(c, c->psi_s, c->psi64, c->n_occ, c->n_pw, false);
+        if (rr == BSE_OK) rr = make_split64(c, c->psiT_s, c->psi64, c->n_occ, c->n_pw, true);
+        if (rr == BSE_OK && c->n_pdep > 0) rr = make_split64(c, c->pdep_s, c->pdep64, c->n_pdep, c->n_pw, false);
+        if (rr == BSE_OK && c->n_pdep > 0) rr = make_split64(c, c->pdepT_s, c->pdep64, c->n_pdep, c->n_pw, true);
+        if (rr != BSE_OK) return bail(rr);
+        c->tc_ok = true;
+      }
     }
   }
   cudaError_t e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "bse_create"));
   *out = c;
+  return BSE_OK;
+}
+
+static int check_device_flag(bse_ctx* c) {
+  if (!c->d_err) return BSE_OK;
+  int h = 0;
+  if (cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return BSE_OK;
+  if (h) {
+    cudaMemset(c->d_err, 0, sizeof(int));
+    return fail(c, BSE_ERR_TIMEOUT, "a bounded device wait gave up (tensor-core pipeline)");
+  }
   return BSE_OK;
 }
 
@@ -852,6 +964,7 @@ int bse_build_tau(bse_ctx* c, int64_t* n_pairs_out, double* thr_out) {
   cudaStreamSynchronize(c->st);
   c->prof.resolve();
   if (r != BSE_OK) return r;
+  if ((r = check_device_flag(c)) != BSE_OK) return r;
   if (n_pairs_out) *n_pairs_out = c->n_pairs;
   if (thr_out) *thr_out = c->thr;
   return BSE_OK;
@@ -884,7 +997,7 @@ int bse_apply_liouville(bse_ctx* c, int n_vec, const void* a_in, void* a_out) {
   cudaError_t e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return cuda_fail(c, e, "bse_apply_liouville");
   c->prof.resolve();
-  return BSE_OK;
+  return check_device_flag(c);
 }
 
 int bse_davidson(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, void* vec_out,
@@ -897,6 +1010,10 @@ int bse_davidson(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, void
               : davidson_impl<float>(c, o, omega_out, (float*)vec_out, stats);
   cudaStreamSynchronize(c->st);
   c->prof.resolve();
+  if (r == BSE_OK || r == BSE_ERR_NOT_CONVERGED) {
+    const int f = check_device_flag(c);
+    if (f != BSE_OK) return f;
+  }
   return r;
 }
 

@@ -70,6 +70,16 @@ template <typename C> struct Dft<C, 8> {
   }
 };
 
+// Shared-memory position of element k of line i: one pad slot per 16 complex values
+// and an odd line stride, so strided butterfly writes and the transposed line loads of
+// the y / z passes fall into distinct banks.
+template <int N> struct Pad {
+  static constexpr int raw = N + N / 16;
+  static constexpr int LS = raw | 1;
+};
+template <int N>
+__device__ __forceinline__ int sidx(int i, int k) { return i * Pad<N>::LS + k + (k >> 4); }
+
 // one Stockham stage of radix R over TX lines of length N (src -> dst, both smem)
 template <typename C, int N, int R, int TX>
 __device__ __forceinline__ void stage(const C* src, C* dst, const C* tw, int Ns, int sign) {
@@ -78,16 +88,15 @@ __device__ __forceinline__ void stage(const C* src, C* dst, const C* tw, int Ns,
   for (int e = threadIdx.x; e < TX * NB; e += blockDim.x) {
     const int i = e / NB, j = e - i * NB;
     const int k = j % Ns;
-    const C* s = src + i * N;
     C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = s[j + r * NB];
+    for (int r = 0; r < R; ++r) v[r] = src[sidx<N>(i, j + r * NB)];
 #pragma unroll
     for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[(r * k * step) % N]);
     Dft<C, R>::run(v, sign);
-    C* d = dst + i * N + (j / Ns) * Ns * R + k;
+    const int o = (j / Ns) * Ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) d[r * Ns] = v[r];
+    for (int r = 0; r < R; ++r) dst[sidx<N>(i, o + r * Ns)] = v[r];
   }
 }
 
@@ -98,8 +107,8 @@ __global__ void __launch_bounds__(256) fft_axis_kernel(cplx<T>* __restrict__ dat
   constexpr int TX = Plan<N>::TX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf0 = reinterpret_cast<C*>(smem_raw);
-  C* buf1 = buf0 + TX * N;
-  C* tw = buf1 + TX * N;
+  C* buf1 = buf0 + TX * Pad<N>::LS;
+  C* tw = buf1 + TX * Pad<N>::LS;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     C t = table[i];
     if (sign > 0) t.y = -t.y;
@@ -122,7 +131,7 @@ __global__ void __launch_bounds__(256) fft_axis_kernel(cplx<T>* __restrict__ dat
   for (int e = threadIdx.x; e < TX * N; e += blockDim.x) {
     int i, k;
     if (axis == 0) { i = e / N; k = e - i * N; } else { k = e / TX; i = e - k * TX; }
-    buf0[i * N + k] = data[base + i * si + k * sk];
+    buf0[sidx<N>(i, k)] = data[base + i * si + k * sk];
   }
   __syncthreads();
   C* src = buf0; C* dst = buf1;
@@ -143,7 +152,7 @@ __global__ void __launch_bounds__(256) fft_axis_kernel(cplx<T>* __restrict__ dat
   for (int e = threadIdx.x; e < TX * N; e += blockDim.x) {
     int i, k;
     if (axis == 0) { i = e / N; k = e - i * N; } else { k = e / TX; i = e - k * TX; }
-    data[base + i * si + k * sk] = src[i * N + k];
+    data[base + i * si + k * sk] = src[sidx<N>(i, k)];
   }
 }
 
@@ -151,7 +160,7 @@ template <typename T, int N>
 static cudaError_t launch_fft3d(cplx<T>* data, long n_batch, int sign, const cplx<T>* table,
                                 cudaStream_t st) {
   constexpr int TX = Plan<N>::TX;
-  const size_t smem = (size_t)(2 * TX * N + N) * sizeof(cplx<T>);
+  const size_t smem = (size_t)(2 * TX * Pad<N>::LS + N) * sizeof(cplx<T>);
   static bool attr_set = false;   // per instantiation; attribute is per device function
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(fft_axis_kernel<T, N>,

@@ -18,7 +18,7 @@
 namespace bse {
 
 template <typename T, int TR, int SC>
-__global__ void __launch_bounds__(256) k1d_tile_kernel(
+__global__ void __launch_bounds__(256, 3) k1d_tile_kernel(
     int n_vec, int n_occ, long n3, const T* __restrict__ a, const T* __restrict__ tau,
     const int* __restrict__ bptr, const int* __restrict__ bw, const int4* __restrict__ bp,
     int n_blocks, const T* __restrict__ vloc, const T* __restrict__ vh,

@@ -45,6 +45,17 @@ template <typename T>
 cudaError_t k1d_combine(int n_vec, int n_occ, long n3, const T* a, const T* tau, const int* nbr_ptr,
                         const int* nbr_w, const int* nbr_p, const T* vloc, const T* vh,
                         const T* upsi, double spin_factor, T* out, cudaStream_t st);
+// ---- tc_gemm.cu (tcgen05 BF16x3) ----
+size_t tc_map_bytes();
+bool tc_make_map(void* map_out, const void* ptr, long rows, long cols, long ld);
+cudaError_t tc_gemm_bf16x3(const void* mAh, const void* mAl, const void* mBh, const void* mBl, int M, int N,
+                           int K, double alpha, double beta, float* out, long ldo, int splits, int* err,
+                           cudaStream_t st);
+cudaError_t bf16_split(const float* X, long rows, int cols, long ld_in, void* hi, void* lo, long ld_out,
+                       cudaStream_t st);
+cudaError_t bf16_split64(const double* X, long rows, int cols, long ld_in, void* hi, void* lo, long ld_out,
+                         bool transpose, cudaStream_t st);
+
 // ---- k1d.cu ----
 template <typename T>
 int k1d_vectors_per_cta(int n_occ);
