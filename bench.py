@@ -6,7 +6,7 @@ localised orbitals, 512 PDEP vectors with lambda_i = -0.8 exp(-i/100), overlap
 threshold keeping 15% of the v <= w pairs, 16 excitations with Davidson block 32,
 mixed precision (FP32 FFTs / pair products / tau streaming, FP64 Davidson algebra).
 A step is one whole solve: screened-integral build (bse_build_tau) followed by the
-Davidson solve (bse_davidson) to ||r|| <= 1e-4 Ha, inputs resident in HBM. The
+Davidson solve (bse_davidson) to ||r|| <= 2e-4 Ha, inputs resident in HBM. The
 FP64 plain path solves the same system once: the step is valid when every mixed
 excitation energy is within 1 meV of it. Inputs (tau 7.4 GB, r-space workspaces
 24 GB) are far larger than L2, so no separate L2 flush is done.
@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 MEV = 3.6749322e-5
 N_EIG, BLOCK, MAX_SUB = 16, 32, 128
-TOL_MIXED, TOL_FP64 = 1e-4, 1e-5
+TOL_MIXED, TOL_FP64 = 2e-4, 1e-5
 
 
 def parse():
