@@ -25,7 +25,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 # every symbol include/bse.h declares
 EXPORTS = ["bse_create", "bse_build_tau", "bse_get_pairs", "bse_get_overlaps",
            "bse_apply_liouville", "bse_davidson", "bse_last_error", "bse_version",
-           "bse_destroy", "bse_profile", "bse_profile_read"]
+           "bse_destroy", "bse_profile", "bse_profile_read", "bse_apply_liouville_static"]
 
 
 class BseError(RuntimeError):
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
     lib.bse_get_pairs.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.bse_get_overlaps.argtypes = [P, C.POINTER(C.c_double)]
     lib.bse_apply_liouville.argtypes = [P, C.c_int, P, P]
+    lib.bse_apply_liouville_static.argtypes = [P, C.c_int, P, P]
     lib.bse_davidson.argtypes = [P, C.POINTER(DavidsonOpts), C.POINTER(C.c_double), P,
                                  C.POINTER(DavidsonStats)]
     lib.bse_last_error.argtypes = [P]
@@ -198,6 +199,15 @@ class Context:
         self._check(self.lib.bse_apply_liouville(self.h, int(a_in.shape[0]),
                                                  C.c_void_p(a_in.data_ptr()),
                                                  C.c_void_p(a_out.data_ptr())))
+        return a_out
+
+    def apply_static(self, a_in, a_out):
+        """The operator with workspaces in the library's fixed device array (no allocation)."""
+        assert a_in.is_contiguous() and a_out.is_contiguous()
+        assert tuple(a_in.shape[1:]) == (self.n_occ, self.n_pw) and a_in.shape == a_out.shape
+        self._check(self.lib.bse_apply_liouville_static(self.h, int(a_in.shape[0]),
+                                                        C.c_void_p(a_in.data_ptr()),
+                                                        C.c_void_p(a_out.data_ptr())))
         return a_out
 
     def davidson(self, n_eig, block, max_sub, max_it=200, res_tol=1e-5, precond=0, vec_out=None,

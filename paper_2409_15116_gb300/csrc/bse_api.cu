@@ -1052,3 +1052,117 @@ int bse_profile_read(bse_ctx* c, bse_prof_entry* out, int cap, int* n_out, int64
 }
 
 }  // extern "C"
+
+// =================================================================================
+// Operator application that allocates nothing (bse_apply_liouville_static).
+//
+// Some callers cannot call cudaMalloc at the moment they need the operator: code that
+// runs while a CUDA graph is being captured, hosts whose memory budget is fixed by an
+// external pool, or hard real-time paths where a device allocation (which may
+// synchronise the device) is not allowed. For them the r-space workspaces of one
+// application live in a fixed array compiled into this library instead of being
+// allocated by the context.
+// =================================================================================
+#include <mutex>
+
+namespace {
+
+constexpr size_t BSE_STATIC_SCRATCH_BYTES = (size_t)32 << 20;   // 32 MiB per device
+
+// held by every GPU that loads this library, for the life of the process
+static __device__ __align__(256) unsigned char g_static_scratch[BSE_STATIC_SCRATCH_BYTES];
+
+std::mutex g_static_mu;
+void* g_static_addr[256] = {};
+
+// device address of the scratch array on the current device (looked up once per device)
+cudaError_t static_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return cudaSuccess;
+}
+
+template <typename T>
+int apply_static_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out, unsigned char* ws) {
+  const long n3 = c->n3;
+  const long nf = n_vec * c->n_occ;
+  const long ngr = (nf + 1) / 2, nh = (n_vec + 1) / 2;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t b_a = up((size_t)ngr * n3 * sizeof(cplx<T>));
+  const size_t b_h = up((size_t)nh * n3 * sizeof(cplx<T>));
+  const size_t b_c = up((size_t)nf * c->n_occ * sizeof(T));
+  const size_t need = 2 * b_a + b_h + b_c;
+  if (need > BSE_STATIC_SCRATCH_BYTES) {
+    char buf[256];
+    snprintf(buf, sizeof(buf),
+             "bse_apply_liouville_static: %ld vectors need %zu bytes of scratch; the static array holds %zu",
+             n_vec, need, BSE_STATIC_SCRATCH_BYTES);
+    return fail(c, BSE_ERR_INVALID_ARG, buf);
+  }
+  cplx<T>* ga = reinterpret_cast<cplx<T>*>(ws);
+  cplx<T>* gr = reinterpret_cast<cplx<T>*>(ws + b_a);
+  cplx<T>* gh = reinterpret_cast<cplx<T>*>(ws + 2 * b_a);
+  T* cb = reinterpret_cast<T*>(ws + 2 * b_a + b_h);
+  const int N = c->N;
+  const double sf = (c->spin == 0) ? 2.0 : 0.0;
+  // the array keeps the previous call's contents: everything read before it is
+  // written is cleared here (the a(r) and Hartree grids, the odd tail of R(r))
+  CK((sphere_unpack<T, T>(a_in, nf, c->n_pw, c->n_half, c->gpos, c->gneg, ga, n3, true, false, c->st)));
+  CK(fft3d<T>(ga, ngr, N, +1, tw_of<T>(c), c->st));
+  CK(cudaMemsetAsync(gh, 0, (size_t)nh * n3 * sizeof(cplx<T>), c->st));
+  if (sf != 0.0) {
+    CK(hartree_density<T>((int)n_vec, c->n_occ, n3, (const T*)ga, upsi_of<T>(c), (T*)gh, c->st));
+    CK(fft3d<T>(gh, nh, N, -1, tw_of<T>(c), c->st));
+    CK(grid_coulomb<T>(gh, nh, N, c->L, c->omega, 0, 1.0 / (double)n3, c->st));
+    CK(fft3d<T>(gh, nh, N, +1, tw_of<T>(c), c->st));
+  }
+  if (nf & 1) CK(cudaMemsetAsync(gr + (ngr - 1) * n3, 0, (size_t)n3 * sizeof(cplx<T>), c->st));
+  if (k1d_vectors_per_cta<T>(c->n_occ) > 0 && n3 % 32 == 0) {
+    CK(k1d_tiled<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, c->bptr, c->bw, c->bp,
+                    c->n_rblocks, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
+  } else {
+    CK(k1d_combine<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, c->nbr_ptr, c->nbr_w,
+                      c->nbr_p, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
+  }
+  CK(fft3d<T>(gr, ngr, N, -1, tw_of<T>(c), c->st));
+  CK((sphere_pack<T, T>(gr, nf, c->n_pw, c->n_half, c->gpos, c->gneg, n3, 1.0 / (double)n3, a_out,
+                        a_in, c->g2p, c->eps, c->scissor, c->n_occ, c->st)));
+  // P_c with the SIMT GEMM (the tensor-core path would allocate split buffers)
+  const T* psi = psi_of<T>(c);
+  CK((gemm<T, T>(false, true, (int)nf, c->n_occ, c->n_pw, 1.0, a_out, c->n_pw, psi, c->n_pw, 0.0, cb,
+                 c->n_occ, 1, c->st)));
+  CK((gemm<T, T>(false, false, (int)nf, c->n_pw, c->n_occ, -1.0, cb, c->n_occ, psi, c->n_pw, 1.0, a_out,
+                 c->n_pw, 1, c->st)));
+  CK(zero_pad_column<T>((int)nf, c->n_pw, a_out, c->st));
+  return BSE_OK;
+}
+
+}  // namespace
+
+extern "C" int bse_apply_liouville_static(bse_ctx* c, int n_vec, const void* a_in, void* a_out) {
+  if (!c) return BSE_ERR_INVALID_ARG;
+  if (n_vec < 0 || (n_vec > 0 && (!a_in || !a_out))) return fail(c, BSE_ERR_INVALID_ARG, "bad apply arguments");
+  if (a_in == a_out && n_vec > 0) return fail(c, BSE_ERR_INVALID_ARG, "a_out must not alias a_in");
+  if (!c->tau_ready) return fail(c, BSE_ERR_STATE, "bse_build_tau must run before bse_apply_liouville_static");
+  if (n_vec == 0) return BSE_OK;
+  void* ws = nullptr;
+  cudaError_t e = static_scratch_address(&ws);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetSymbolAddress of the static scratch");
+  int r = (c->prec == BSE_PREC_FP64)
+              ? apply_static_impl<double>(c, n_vec, (const double*)a_in, (double*)a_out, (unsigned char*)ws)
+              : apply_static_impl<float>(c, n_vec, (const float*)a_in, (float*)a_out, (unsigned char*)ws);
+  if (r != BSE_OK) return r;
+  e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "bse_apply_liouville_static");
+  return BSE_OK;
+}
