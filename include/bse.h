@@ -136,7 +136,9 @@ typedef struct {
   int max_it;       /* iteration limit */
   double res_tol;   /* converged when every ||L x - theta x||_2 <= res_tol (Ha) */
   int precond;      /* 0 diagonal: t = P_c r / max(1/2|G|^2 + V(0) + Delta - eps_v - theta, 0.1 Ha);
-                       1 learned (falls back to diagonal if no net loaded) */
+                       1 learned (bse_precond_load); the diagonal step replaces it when no
+                       network is loaded, on a non-finite output, and for good once the largest
+                       residual gains less than 1% over eight iterations */
 } bse_davidson_opts;
 
 typedef struct {
@@ -154,6 +156,44 @@ typedef struct {
  * On BSE_ERR_NOT_CONVERGED omega_out, vec_out and stats hold the last Ritz pairs. */
 int bse_davidson(bse_ctx* ctx, const bse_davidson_opts* opts, double* omega_out,
                  void* vec_out, bse_davidson_stats* stats);
+
+/* ---- Learned Davidson preconditioner (library addition; the paper's Davidson of
+ * Section 3 has no learned component). A per-element MLP 5 -> 64 -> 64 -> 1 rescales the
+ * diagonal step: features f = (1/2|G|^2, eps_v, theta, d - theta, r_e sqrt(dim)/||r||),
+ * x = (f - mu)/sigma, h1 = act(relu(W1 x + b1)), h2 = act(relu(W2 h1 + b2)),
+ * o = w3.h2 + b3, t = P_c(exp(clip(o,-8,8)) r / max(d - theta, 0.1 Ha)), with
+ * d = 1/2|G|^2 + V(0) + Delta - eps_v and act = bfloat16 rounding (FP32 weights, BF16
+ * activations). A zero last layer is the diagonal preconditioner. Parameters: float
+ * [BSE_PRECOND_NPARAM] = W1[64x5] b1[64] W2[64x64] b2[64] w3[64] b3 mu[5] sigma[5].
+ * Loss over samples (theta, r, t*): the scale-free misfit mean(1 - <y,t*>^2/(|y|^2 |t*|^2)),
+ * y = P_c(g r) -- Davidson keeps only a correction's direction. ---- */
+#define BSE_PRECOND_NPARAM 4619
+
+/* Runs the plain solver twice on an FP64 context: once to ref_eig (<= 32) eigenpairs
+ * (res_tol 1e-8), once with opts (diagonal preconditioner), capturing up to max_samples
+ * (residual, Ritz value, Ritz vector) triples of the corrections it computes. Targets
+ * are the exact shifted-inverse (Jacobi-Davidson) corrections t* = y/(u.y) - u with
+ * y = sum_j x_j (x_j.u)/(lambda_j - theta) over the reference pairs. Replaces the
+ * context's samples; *n_out (nullable) receives their number. */
+int bse_precond_collect(bse_ctx* ctx, const bse_davidson_opts* opts, int ref_eig, int max_samples,
+                        int* n_out);
+
+/* Replaces the context's samples with caller data: host [n][n_occ][n_pw] residuals r and
+ * targets t, host [n] Ritz values theta (FP64). */
+int bse_precond_set_samples(bse_ctx* ctx, int n, const double* r, const double* t, const double* theta);
+
+/* Loss and gradient (host double [BSE_PRECOND_NPARAM]; mu, sigma entries 0) of the
+ * parameters over the context's samples; act_bf16 selects bfloat16 activations. */
+int bse_precond_grad(bse_ctx* ctx, const float* params, int act_bf16, double* loss_out, double* grad_out);
+
+/* Adam training on the GPU over the samples of n_ctx contexts (one step per context per
+ * epoch), starting from init; mu and sigma are set from the samples' feature moments.
+ * params_out: host float [BSE_PRECOND_NPARAM]; loss_hist (nullable): host [epochs]. */
+int bse_precond_train(bse_ctx* const* ctxs, int n_ctx, const float* init, int epochs, double lr,
+                      int act_bf16, float* params_out, double* loss_hist);
+
+/* Installs (or with NULL removes) the network used by bse_davidson when opts.precond = 1. */
+int bse_precond_load(bse_ctx* ctx, const float* params);
 
 /* Per-region profile (library addition; the paper reports module wall times only,
  * Fig. 3). When enabled, each instrumented region of the hot path is bracketed by

@@ -25,7 +25,10 @@ PREC_FP64, PREC_MIXED = 0, 1
 # every symbol include/bse.h declares
 EXPORTS = ["bse_create", "bse_build_tau", "bse_get_pairs", "bse_get_overlaps",
            "bse_apply_liouville", "bse_davidson", "bse_last_error", "bse_version",
-           "bse_destroy", "bse_profile", "bse_profile_read", "bse_apply_liouville_static"]
+           "bse_destroy", "bse_profile", "bse_profile_read", "bse_apply_liouville_static",
+           "bse_precond_collect", "bse_precond_set_samples", "bse_precond_grad",
+           "bse_precond_train", "bse_precond_load"]
+NPARAM = 4619
 
 
 class BseError(RuntimeError):
@@ -86,6 +89,13 @@ def load(path: str = LIB_PATH):
     lib.bse_profile.argtypes = [P, C.c_int]
     lib.bse_profile_read.argtypes = [P, C.POINTER(ProfEntry), C.c_int, C.POINTER(C.c_int),
                                      C.POINTER(C.c_int64)]
+    D = C.POINTER(C.c_double)
+    F = C.POINTER(C.c_float)
+    lib.bse_precond_collect.argtypes = [P, C.POINTER(DavidsonOpts), C.c_int, C.c_int, C.POINTER(C.c_int)]
+    lib.bse_precond_set_samples.argtypes = [P, C.c_int, D, D, D]
+    lib.bse_precond_grad.argtypes = [P, F, C.c_int, D, D]
+    lib.bse_precond_train.argtypes = [C.POINTER(P), C.c_int, F, C.c_int, C.c_double, C.c_int, F, D]
+    lib.bse_precond_load.argtypes = [P, F]
     lib.bse_destroy.argtypes = [P]
     lib.bse_destroy.restype = None
     for name in EXPORTS:
@@ -201,6 +211,37 @@ class Context:
                                                  C.c_void_p(a_out.data_ptr())))
         return a_out
 
+    # ---- learned preconditioner ----
+    def precond_collect(self, n_eig, block, max_sub, max_it=200, res_tol=1e-6, ref_eig=32,
+                        max_samples=256):
+        opts = DavidsonOpts(n_eig=n_eig, block=block, max_sub=max_sub, max_it=max_it,
+                            res_tol=res_tol, precond=0)
+        n = C.c_int()
+        self._check(self.lib.bse_precond_collect(self.h, C.byref(opts), ref_eig, max_samples, C.byref(n)))
+        return int(n.value)
+
+    def precond_set_samples(self, r, t, theta):
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        self._check(self.lib.bse_precond_set_samples(self.h, int(th.size), _dptr(r), _dptr(t), _dptr(th)))
+
+    def precond_grad(self, params, act_bf16=False):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        g = np.zeros(NPARAM)
+        loss = C.c_double()
+        self._check(self.lib.bse_precond_grad(self.h, p.ctypes.data_as(C.POINTER(C.c_float)),
+                                              int(act_bf16), C.byref(loss), _dptr(g)))
+        return float(loss.value), g
+
+    def precond_load(self, params):
+        if params is None:
+            self._check(self.lib.bse_precond_load(self.h, None))
+            return
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._keep_params = p
+        self._check(self.lib.bse_precond_load(self.h, p.ctypes.data_as(C.POINTER(C.c_float))))
+
     def apply_static(self, a_in, a_out):
         """The operator with workspaces in the library's fixed device array (no allocation)."""
         assert a_in.is_contiguous() and a_out.is_contiguous()
@@ -227,6 +268,33 @@ class Context:
 
 def version() -> str:
     return load().bse_version().decode()
+
+
+def precond_train(contexts, init, epochs=40, lr=3e-3, act_bf16=True):
+    """Adam training on the GPU over the samples of several contexts; returns (params, losses)."""
+    lib = load()
+    hs = (C.c_void_p * len(contexts))(*[c.h.value for c in contexts])
+    p0 = np.ascontiguousarray(init, dtype=np.float32)
+    out = np.zeros(NPARAM, dtype=np.float32)
+    hist = np.zeros(epochs)
+    rc = lib.bse_precond_train(hs, len(contexts), p0.ctypes.data_as(C.POINTER(C.c_float)), epochs,
+                               float(lr), int(act_bf16), out.ctypes.data_as(C.POINTER(C.c_float)),
+                               _dptr(hist))
+    if rc != BSE_OK:
+        raise BseError(rc, lib.bse_last_error(contexts[0].h).decode())
+    return out, hist
+
+
+def precond_init(seed=0):
+    """He-normal hidden layers, zero last layer (the untrained network is the diagonal step)."""
+    rng = np.random.default_rng(seed)
+    H, F = 64, 5
+    p = np.zeros(NPARAM, dtype=np.float32)
+    p[:H * F] = rng.standard_normal(H * F) * np.sqrt(2.0 / F)
+    o = H * F + H
+    p[o:o + H * H] = rng.standard_normal(H * H) * np.sqrt(2.0 / H)
+    p[-5:] = 1.0
+    return p
 
 
 def launch_count() -> int:

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <queue>
 #include <string>
@@ -74,6 +75,11 @@ struct bse_ctx {
   void *ws_ahi = nullptr, *ws_alo = nullptr, *ws_bhi = nullptr, *ws_blo = nullptr;
   long ws_split_rows = 0;
   int* d_err = nullptr;
+  // learned preconditioner: inference weights and training samples
+  float* lp_params = nullptr;
+  int* d_bad = nullptr;
+  long lp_ns = 0;                      // samples held
+  double *lp_r = nullptr, *lp_t = nullptr, *lp_theta = nullptr, *lp_rn2 = nullptr, *lp_tn2 = nullptr;
   // problem
   int N = 0;
   long n3 = 0;
@@ -537,9 +543,15 @@ int build_tau_impl(bse_ctx* c) {
 // ---------------------------------------------------------------------------------
 struct Cand { double d; long flat; };
 
+// called each iteration with the Ritz vectors X, residuals R (device, kk rows), the Ritz
+// values and the indices that receive corrections
+template <typename T>
+using SampleHook = std::function<int(int, const T*, const T*, const std::vector<double>&,
+                                     const std::vector<int>&)>;
+
 template <typename T>
 int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* vec_out,
-                  bse_davidson_stats* stats) {
+                  bse_davidson_stats* stats, const SampleHook<T>* hook = nullptr) {
   using clk = std::chrono::steady_clock;
   const auto t_start = clk::now();
   const int ne = o->n_eig, b = o->block, ms = o->max_sub;
@@ -662,6 +674,9 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
   bool converged = false;
   std::vector<double> th(ms), rn(ms);
   int kk = 0;
+  bool use_learned = (o->precond == 1) && c->lp_params != nullptr;
+  int fallbacks = (o->precond == 1 && c->lp_params == nullptr) ? 1 : 0;
+  std::vector<double> res_hist;
   while (true) {
     ++it;
     // the k lowest Ritz pairs are all the algebra needs: n_eig for the residuals and
@@ -690,15 +705,41 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
       rn[i] = std::sqrt(rn[i]);
       if (rn[i] > o->res_tol && (int)todo.size() < b) todo.push_back(i);
     }
+    if (hook && !todo.empty()) CA((*hook)(kk, X, Rr, th, todo));
     if (kk == ne && todo.empty()) { converged = true; break; }
     if (it >= o->max_it) break;
     int nt = (int)todo.size();
     if (nt == 0) break;
     CK(cudaMemcpyAsync(which, todo.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, c->st));
+    // learned preconditioner with the diagonal one as fallback: on a non-finite output,
+    // and for good once the residuals stagnate (no 1% gain of the largest residual over
+    // eight iterations)
+    {
+      double rmax = 0;
+      for (int i = 0; i < kk; ++i) rmax = std::max(rmax, rn[i]);
+      res_hist.push_back(rmax);
+      if (use_learned && res_hist.size() > 8) {
+        double before = 1e300, recent = 1e300;
+        for (size_t q = 0; q + 8 < res_hist.size(); ++q) before = std::min(before, res_hist[q]);
+        for (size_t q = res_hist.size() - 8; q < res_hist.size(); ++q) recent = std::min(recent, res_hist[q]);
+        if (recent > 0.99 * before) { use_learned = false; ++fallbacks; }
+      }
+    }
     {
       Scope sc(c, "davidson_precond", 2.0 * nt * (double)dim * sizeof(T), 4.0 * nt * c->n_occ * (double)dim);
-      CK(precond_diag<T>(nt, c->n_occ, c->n_pw, Rr, theta, which, c->g2p, c->eps, c->v0, c->scissor,
-                         Tt, c->st));
+      bool diag = !use_learned;
+      if (use_learned) {
+        CK(cudaMemsetAsync(c->d_bad, 0, sizeof(int), c->st));
+        CK(precond_learned<T>(nt, c->n_occ, c->n_pw, c->lp_params, Rr, theta, nrm, which, c->g2p,
+                              c->eps, c->v0, c->scissor, Tt, c->d_bad, c->st));
+        int hb = 0;
+        CK(cudaMemcpyAsync(&hb, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        if (hb) { diag = true; ++fallbacks; }
+      }
+      if (diag)
+        CK(precond_diag<T>(nt, c->n_occ, c->n_pw, Rr, theta, which, c->g2p, c->eps, c->v0, c->scissor,
+                           Tt, c->st));
       CA(proj(nt, Tt));
     }
     if (m + nt > ms) {
@@ -793,7 +834,7 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
     double mx = 0;
     for (int i = 0; i < kk; ++i) mx = std::max(mx, rn[i]);
     stats->res_max = mx;
-    stats->precond_fallbacks = 0;
+    stats->precond_fallbacks = fallbacks;
   }
   if (!converged) return fail(c, BSE_ERR_NOT_CONVERGED, "Davidson did not converge within max_it");
   return BSE_OK;
@@ -912,6 +953,10 @@ int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) 
   std::vector<float2> twf(tw.size());
   for (size_t i = 0; i < tw.size(); ++i) { twf[i].x = (float)tw[i].x; twf[i].y = (float)tw[i].y; }
   UPLOAD(c->tw32, twf.data(), twf.size());
+  {
+    int r0 = dalloc(c, &c->d_bad, 1);
+    if (r0 != BSE_OK) return bail(r0);
+  }
   // psi_v(r) (times Omega^{1/2}) in FP64 on the grid, pair layout
   {
     const long ng = (c->n_occ + 1) / 2;
@@ -1048,6 +1093,265 @@ int bse_profile_read(bse_ctx* c, bse_prof_entry* out, int cap, int* n_out, int64
     for (int i = 0; i < cap && i < (int)c->prof.acc.size(); ++i) out[i] = c->prof.acc[i];
   if (n_out) *n_out = (int)c->prof.acc.size();
   if (launches) *launches = (int64_t)launch_count();
+  return BSE_OK;
+}
+
+}  // extern "C"
+
+// =================================================================================
+// Learned preconditioner: samples, loss/gradient, training, loading
+// =================================================================================
+namespace {
+
+void lp_free_samples(bse_ctx* c) {
+  dfree(c, c->lp_r); dfree(c, c->lp_t); dfree(c, c->lp_theta); dfree(c, c->lp_rn2); dfree(c, c->lp_tn2);
+  c->lp_r = c->lp_t = c->lp_theta = c->lp_rn2 = c->lp_tn2 = nullptr;
+  c->lp_ns = 0;
+}
+
+int lp_alloc_samples(bse_ctx* c, long ns) {
+  lp_free_samples(c);
+  const long dim = (long)c->n_occ * c->n_pw;
+  CA(dalloc(c, &c->lp_r, (size_t)ns * dim));
+  CA(dalloc(c, &c->lp_t, (size_t)ns * dim));
+  CA(dalloc(c, &c->lp_theta, (size_t)ns));
+  CA(dalloc(c, &c->lp_rn2, (size_t)ns));
+  CA(dalloc(c, &c->lp_tn2, (size_t)ns));
+  c->lp_ns = ns;
+  return BSE_OK;
+}
+
+int lp_finish_samples(bse_ctx* c) {
+  const long dim = (long)c->n_occ * c->n_pw;
+  CK(row_norms2<double>((int)c->lp_ns, dim, c->lp_r, c->lp_rn2, c->st));
+  CK(row_norms2<double>((int)c->lp_ns, dim, c->lp_t, c->lp_tn2, c->st));
+  return BSE_OK;
+}
+
+// one pass over the context's samples: loss (mean over samples, times `weight`) into d_loss
+// and its gradient added into d_grad (double, mlpl::N)
+int lp_step(bse_ctx* c, const float* d_params, int bf, double* d_grad, double* d_loss) {
+  using namespace mlpl;
+  const long ns = c->lp_ns, dim = (long)c->n_occ * c->n_pw, rows = ns * dim;
+  std::vector<void*> tmp;
+  auto al = [&](auto** p, size_t n) { int r = dalloc(c, p, n); if (r == BSE_OK) tmp.push_back(*p); return r; };
+  struct G2 { bse_ctx* c; std::vector<void*>* t; ~G2() { for (void* p : *t) dfree(c, p); } } guard{c, &tmp};
+  float *X, *H1, *H2, *O, *DO, *DZ1, *DZ2, *ones;
+  double *Gv, *Y, *dg, *cb, *gpart, *ab, *bb;
+  CA(al(&X, (size_t)rows * F)); CA(al(&H1, (size_t)rows * H)); CA(al(&H2, (size_t)rows * H));
+  CA(al(&O, (size_t)rows)); CA(al(&DO, (size_t)rows)); CA(al(&DZ1, (size_t)rows * H));
+  CA(al(&DZ2, (size_t)rows * H)); CA(al(&ones, (size_t)rows)); CA(al(&Gv, (size_t)rows));
+  CA(al(&Y, (size_t)rows)); CA(al(&dg, (size_t)rows)); CA(al(&gpart, (size_t)N));
+  CA(al(&cb, (size_t)ns * c->n_occ * c->n_occ));
+  CA(al(&ab, (size_t)2 * ns)); CA(al(&bb, (size_t)ns));
+  std::vector<float> h1(rows, 1.0f);
+  CK(cudaMemcpyAsync(ones, h1.data(), sizeof(float) * rows, cudaMemcpyHostToDevice, c->st));
+  CK(mlp_train_forward(d_params, rows, c->n_occ, c->n_pw, c->lp_r, c->lp_theta, c->lp_rn2, c->g2p,
+                       c->eps, c->v0, c->scissor, bf, X, H1, H2, O, Gv, Y, c->st));
+  CA(project<double>(c, ns * c->n_occ, Y, cb));        // Y <- P_c(g r)
+  // per sample a = <y, t*> and b = |y|^2, interleaved as (a, b)
+  CK(row_dots((int)ns, dim, Y, c->lp_t, bb, c->st));
+  CK(cudaMemcpy2DAsync(ab, 2 * sizeof(double), bb, sizeof(double), sizeof(double), ns, cudaMemcpyDeviceToDevice, c->st));
+  CK(row_norms2<double>((int)ns, dim, Y, bb, c->st));
+  CK(cudaMemcpy2DAsync(ab + 1, 2 * sizeof(double), bb, sizeof(double), sizeof(double), ns, cudaMemcpyDeviceToDevice, c->st));
+  CK(mlp_loss(rows, dim, Y, c->lp_t, c->lp_tn2, ab, c->lp_r, 1.0 / (double)ns, dg, d_loss, c->st));
+  CK(mlp_train_backward(d_params, rows, H1, H2, O, Gv, dg, DO, DZ1, DZ2, c->st));
+  CK(cudaMemsetAsync(gpart, 0, sizeof(double) * N, c->st));
+  CK((gemm<float, double>(true, false, H, F, (int)rows, 1.0, DZ1, H, X, F, 0.0, gpart + W1, F, 0, c->st)));
+  CK((gemm<float, double>(true, false, 1, H, (int)rows, 1.0, ones, 1, DZ1, H, 0.0, gpart + B1, H, 0, c->st)));
+  CK((gemm<float, double>(true, false, H, H, (int)rows, 1.0, DZ2, H, H1, H, 0.0, gpart + W2, H, 0, c->st)));
+  CK((gemm<float, double>(true, false, 1, H, (int)rows, 1.0, ones, 1, DZ2, H, 0.0, gpart + B2, H, 0, c->st)));
+  CK((gemm<float, double>(true, false, 1, H, (int)rows, 1.0, DO, 1, H2, H, 0.0, gpart + W3, H, 0, c->st)));
+  CK((gemm<float, double>(true, false, 1, 1, (int)rows, 1.0, ones, 1, DO, 1, 0.0, gpart + B3, 1, 0, c->st)));
+  // d_grad += gpart
+  {
+    std::vector<double> hp(N), hg(N);
+    CK(cudaMemcpyAsync(hp.data(), gpart, sizeof(double) * N, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(hg.data(), d_grad, sizeof(double) * N, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int i = 0; i < N; ++i) hg[i] += hp[i];
+    CK(cudaMemcpyAsync(d_grad, hg.data(), sizeof(double) * N, cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+  }
+  return BSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bse_precond_set_samples(bse_ctx* c, int n, const double* r, const double* t, const double* theta) {
+  if (!c) return BSE_ERR_INVALID_ARG;
+  if (n < 1 || !r || !t || !theta) return fail(c, BSE_ERR_INVALID_ARG, "bse_precond_set_samples: bad arguments");
+  const long dim = (long)c->n_occ * c->n_pw;
+  if (!all_finite(r, n * dim) || !all_finite(t, n * dim) || !all_finite(theta, n))
+    return fail(c, BSE_ERR_NUMERIC, "non-finite training sample");
+  CA(lp_alloc_samples(c, n));
+  CK(cudaMemcpyAsync(c->lp_r, r, sizeof(double) * n * dim, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->lp_t, t, sizeof(double) * n * dim, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->lp_theta, theta, sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
+  CA(lp_finish_samples(c));
+  CK(cudaStreamSynchronize(c->st));
+  return BSE_OK;
+}
+
+int bse_precond_collect(bse_ctx* c, const bse_davidson_opts* o, int ref_eig, int max_samples, int* n_out) {
+  if (!c) return BSE_ERR_INVALID_ARG;
+  if (!o || ref_eig < 1 || ref_eig > 32 || max_samples < 1)
+    return fail(c, BSE_ERR_INVALID_ARG, "bse_precond_collect: need options, 1 <= ref_eig <= 32, max_samples >= 1");
+  if (c->prec != BSE_PREC_FP64) return fail(c, BSE_ERR_STATE, "bse_precond_collect needs an FP64 context");
+  if (!c->tau_ready) return fail(c, BSE_ERR_STATE, "bse_build_tau must run first");
+  const long dim = (long)c->n_occ * c->n_pw;
+  // reference eigenpairs of the plain solver
+  double *Xr, *lam;
+  CA(dalloc(c, &Xr, (size_t)ref_eig * dim));
+  CA(dalloc(c, &lam, (size_t)ref_eig));
+  struct G3 { bse_ctx* c; void* a; void* b; ~G3() { dfree(c, a); dfree(c, b); } } g3{c, Xr, lam};
+  bse_davidson_opts ro{ref_eig, std::max(8, ref_eig), std::min(160, 4 * ref_eig + 32), 1000, 1e-8, 0};
+  std::vector<double> lh(ref_eig);
+  int r = davidson_impl<double>(c, &ro, lh.data(), Xr, nullptr);
+  if (r != BSE_OK) return r;
+  CK(cudaMemcpyAsync(lam, lh.data(), sizeof(double) * ref_eig, cudaMemcpyHostToDevice, c->st));
+  // sampling run with the diagonal preconditioner: residuals, Ritz vectors and values
+  double *U, *R;
+  CA(dalloc(c, &U, (size_t)max_samples * dim));
+  CA(dalloc(c, &R, (size_t)max_samples * dim));
+  struct G4 { bse_ctx* c; void* a; void* b; ~G4() { dfree(c, a); dfree(c, b); } } g4{c, U, R};
+  std::vector<double> thetas;
+  SampleHook<double> hook = [&](int, const double* X, const double* Rr, const std::vector<double>& th,
+                                const std::vector<int>& todo) -> int {
+    for (int i : todo) {
+      if ((long)thetas.size() >= max_samples) break;
+      const long s = (long)thetas.size();
+      CK(cudaMemcpyAsync(U + s * dim, X + (long)i * dim, sizeof(double) * dim, cudaMemcpyDeviceToDevice, c->st));
+      CK(cudaMemcpyAsync(R + s * dim, Rr + (long)i * dim, sizeof(double) * dim, cudaMemcpyDeviceToDevice, c->st));
+      thetas.push_back(th[i]);
+    }
+    return BSE_OK;
+  };
+  bse_davidson_opts so = *o;
+  so.precond = 0;
+  std::vector<double> om(so.n_eig);
+  r = davidson_impl<double>(c, &so, om.data(), nullptr, nullptr, &hook);
+  if (r != BSE_OK && r != BSE_ERR_NOT_CONVERGED) return r;
+  const int ns = (int)thetas.size();
+  if (ns == 0) return fail(c, BSE_ERR_STATE, "no samples: the solver converged before any correction");
+  // targets t* = y/(u.y) - u with y = sum_j x_j (x_j . u)/(lambda_j - theta)
+  CA(lp_alloc_samples(c, ns));
+  double *Cm, *uy, *th_d;
+  CA(dalloc(c, &Cm, (size_t)ns * ref_eig));
+  CA(dalloc(c, &uy, (size_t)ns));
+  CA(dalloc(c, &th_d, (size_t)ns));
+  struct G5 { bse_ctx* c; void* a; void* b; void* d; ~G5() { dfree(c, a); dfree(c, b); dfree(c, d); } } g5{c, Cm, uy, th_d};
+  CK(cudaMemcpyAsync(th_d, thetas.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, c->st));
+  CK((gemm<double, double>(false, true, ns, ref_eig, (int)dim, 1.0, U, dim, Xr, dim, 0.0, Cm, ref_eig, 0, c->st)));
+  CK(shift_scale(ns, ref_eig, Cm, lam, th_d, c->st));
+  CK((gemm<double, double>(false, false, ns, (int)dim, ref_eig, 1.0, Cm, ref_eig, Xr, dim, 0.0, c->lp_t, dim, 1, c->st)));
+  CK(row_dots(ns, dim, U, c->lp_t, uy, c->st));
+  CK(jd_targets(ns, dim, c->lp_t, U, uy, c->lp_t, c->st));
+  {
+    double* cb;
+    CA(dalloc(c, &cb, (size_t)ns * c->n_occ * c->n_occ));
+    int rp = project<double>(c, (long)ns * c->n_occ, c->lp_t, cb);
+    dfree(c, cb);
+    if (rp != BSE_OK) return rp;
+  }
+  CK(cudaMemcpyAsync(c->lp_r, R, sizeof(double) * ns * dim, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemcpyAsync(c->lp_theta, th_d, sizeof(double) * ns, cudaMemcpyDeviceToDevice, c->st));
+  CA(lp_finish_samples(c));
+  CK(cudaStreamSynchronize(c->st));
+  if (n_out) *n_out = ns;
+  return BSE_OK;
+}
+
+int bse_precond_grad(bse_ctx* c, const float* params, int act_bf16, double* loss_out, double* grad_out) {
+  if (!c) return BSE_ERR_INVALID_ARG;
+  if (!params || !grad_out) return fail(c, BSE_ERR_INVALID_ARG, "bse_precond_grad: null params or grad_out");
+  if (c->lp_ns == 0) return fail(c, BSE_ERR_STATE, "no training samples on this context");
+  using namespace mlpl;
+  float* dp;
+  double *dgr, *dl;
+  CA(dalloc(c, &dp, N)); CA(dalloc(c, &dgr, N)); CA(dalloc(c, &dl, 1));
+  struct G6 { bse_ctx* c; void* a; void* b; void* d; ~G6() { dfree(c, a); dfree(c, b); dfree(c, d); } } g6{c, dp, dgr, dl};
+  CK(cudaMemcpyAsync(dp, params, sizeof(float) * N, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemsetAsync(dgr, 0, sizeof(double) * N, c->st));
+  CK(cudaMemsetAsync(dl, 0, sizeof(double), c->st));
+  CA(lp_step(c, dp, act_bf16 ? 1 : 0, dgr, dl));
+  double l = 0;
+  CK(cudaMemcpyAsync(grad_out, dgr, sizeof(double) * N, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(&l, dl, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (loss_out) *loss_out = l;
+  return BSE_OK;
+}
+
+int bse_precond_train(bse_ctx* const* ctxs, int n_ctx, const float* init, int epochs, double lr,
+                      int act_bf16, float* params_out, double* loss_hist) {
+  if (!ctxs || n_ctx < 1 || !init || epochs < 1 || !(lr > 0) || !params_out) return BSE_ERR_INVALID_ARG;
+  for (int i = 0; i < n_ctx; ++i)
+    if (!ctxs[i] || ctxs[i]->lp_ns == 0) return ctxs[i] ? fail(ctxs[i], BSE_ERR_STATE, "context without training samples") : BSE_ERR_INVALID_ARG;
+  using namespace mlpl;
+  bse_ctx* c = ctxs[0];
+  // feature standardisation from all samples
+  double* mom;
+  CA(dalloc(c, &mom, 2 * F));
+  CK(cudaMemsetAsync(mom, 0, sizeof(double) * 2 * F, c->st));
+  double nrows = 0;
+  for (int i = 0; i < n_ctx; ++i) {
+    bse_ctx* q = ctxs[i];
+    const long rows = q->lp_ns * (long)q->n_occ * q->n_pw;
+    CK(cudaStreamSynchronize(q->st));
+    CK(feature_moments(rows, q->n_occ, q->n_pw, q->lp_r, q->lp_theta, q->lp_rn2, q->g2p, q->eps, q->v0,
+                       q->scissor, mom, c->st));
+    nrows += (double)rows;
+  }
+  std::vector<double> hm(2 * F);
+  CK(cudaMemcpyAsync(hm.data(), mom, sizeof(double) * 2 * F, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  dfree(c, mom);
+  std::vector<float> p(init, init + N);
+  for (int k = 0; k < F; ++k) {
+    const double mu = hm[k] / nrows;
+    const double var = std::max(hm[F + k] / nrows - mu * mu, 0.0);
+    p[MU + k] = (float)mu;
+    p[SG + k] = (float)std::max(std::sqrt(var), 1e-6);
+  }
+  float *dp, *m, *v;
+  double *dg, *dl;
+  CA(dalloc(c, &dp, N)); CA(dalloc(c, &m, N)); CA(dalloc(c, &v, N)); CA(dalloc(c, &dg, N)); CA(dalloc(c, &dl, 1));
+  struct G7 { bse_ctx* c; std::vector<void*> v; ~G7() { for (void* x : v) dfree(c, x); } } g7{c, {dp, m, v, dg, dl}};
+  CK(cudaMemcpyAsync(dp, p.data(), sizeof(float) * N, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemsetAsync(m, 0, sizeof(float) * N, c->st));
+  CK(cudaMemsetAsync(v, 0, sizeof(float) * N, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  int step = 0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    double total = 0;
+    for (int i = 0; i < n_ctx; ++i) {
+      bse_ctx* q = ctxs[i];
+      CK(cudaMemsetAsync(dg, 0, sizeof(double) * N, q->st));
+      CK(cudaMemsetAsync(dl, 0, sizeof(double), q->st));
+      CA(lp_step(q, dp, act_bf16 ? 1 : 0, dg, dl));
+      CK(adam_step(MU, dp, dg, m, v, (float)lr, ++step, q->st));
+      double l = 0;
+      CK(cudaMemcpyAsync(&l, dl, sizeof(double), cudaMemcpyDeviceToHost, q->st));
+      CK(cudaStreamSynchronize(q->st));
+      total += l / n_ctx;
+    }
+    if (loss_hist) loss_hist[ep] = total;
+  }
+  CK(cudaMemcpy(params_out, dp, sizeof(float) * N, cudaMemcpyDeviceToHost));
+  return BSE_OK;
+}
+
+int bse_precond_load(bse_ctx* c, const float* params) {
+  if (!c) return BSE_ERR_INVALID_ARG;
+  if (!params) { dfree(c, c->lp_params); c->lp_params = nullptr; return BSE_OK; }
+  for (int i = 0; i < mlpl::N; ++i)
+    if (!std::isfinite(params[i])) return fail(c, BSE_ERR_NUMERIC, "non-finite preconditioner parameter");
+  if (!c->lp_params) CA(dalloc(c, &c->lp_params, mlpl::N));
+  CK(cudaMemcpyAsync(c->lp_params, params, sizeof(float) * mlpl::N, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
   return BSE_OK;
 }
 

@@ -56,6 +56,37 @@ cudaError_t bf16_split(const float* X, long rows, int cols, long ld_in, void* hi
 cudaError_t bf16_split64(const double* X, long rows, int cols, long ld_in, void* hi, void* lo, long ld_out,
                          bool transpose, cudaStream_t st);
 
+// ---- precond.cu (learned preconditioner) ----
+// parameter layout: W1[H x F] b1[H] W2[H x H] b2[H] w3[H] b3 mu[F] sigma[F]
+namespace mlpl {
+constexpr int H = 64, F = 5, W1 = 0, B1 = W1 + H * F, W2 = B1 + H, B2 = W2 + H * H, W3 = B2 + H,
+              B3 = W3 + H, MU = B3 + 1, SG = MU + F, N = SG + F;
+}
+template <typename T>
+cudaError_t precond_learned(int k, int n_occ, int n_pw, const float* params, const T* R,
+                            const double* theta, const double* rnorm2, const int* which,
+                            const double* g2p, const double* eps, double v0, double shift, T* out,
+                            int* bad, cudaStream_t st);
+cudaError_t mlp_train_forward(const float* params, long rows, int n_occ, int n_pw, const double* r,
+                              const double* theta, const double* rnorm2, const double* g2p,
+                              const double* eps, double v0, double shift, int bf, float* X, float* H1,
+                              float* H2, float* O, double* G, double* Y, cudaStream_t st);
+cudaError_t mlp_loss(long rows, long dim, const double* py, const double* tstar, const double* tn2,
+                     const double* ab, const double* r, double inv_n, double* dg, double* loss,
+                     cudaStream_t st);
+cudaError_t mlp_train_backward(const float* params, long rows, const float* H1, const float* H2,
+                               const float* O, const double* G, const double* dg, float* DO,
+                               float* DZ1, float* DZ2, cudaStream_t st);
+cudaError_t adam_step(int n_train, float* p, const double* g, float* m, float* v, float lr, int step,
+                      cudaStream_t st);
+cudaError_t feature_moments(long rows, int n_occ, int n_pw, const double* r, const double* theta,
+                            const double* rnorm2, const double* g2p, const double* eps, double v0,
+                            double shift, double* mom, cudaStream_t st);
+cudaError_t jd_targets(int ns, long dim, const double* Y, const double* U, const double* uy, double* T,
+                       cudaStream_t st);
+cudaError_t shift_scale(int ns, int nr, double* C, const double* lam, const double* th, cudaStream_t st);
+cudaError_t row_dots(int ns, long dim, const double* A, const double* B, double* out, cudaStream_t st);
+
 // ---- k1d.cu ----
 template <typename T>
 int k1d_vectors_per_cta(int n_occ);
