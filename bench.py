@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--apply-only", action="store_true",
                     help="time bse_apply_liouville alone on --nvec vectors (operator GB/s)")
     ap.add_argument("--nvec", type=int, default=32)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="solve this many uneven systems of the batch family together (bse_solve_batch)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     return ap.parse_args()
 
@@ -154,6 +156,57 @@ def cpu_oracle_sample(inst, n_apply_vectors: int, budget_s: float):
 
 
 # --------------------------------------------------------------------------------------
+def batch_mode(args, binding, Context, PREC_MIXED, PREC_FP64):
+    """Many independent systems (grids 32/48/64^3, N_occ 32..192, N_pdep = 2 N_occ, 8 VEEs
+    each), one context and CUDA stream per system, solved together by bse_solve_batch; the
+    same systems solved one after another for comparison; FP64 check on the first four."""
+    import numpy as np
+    import torch
+    from synth.instance import make_batched_member
+    systems = [make_batched_member(300 + i) for i in range(args.batch)]
+    n_eig, block, max_sub = 8, 8, 32
+
+    def run_batch():
+        streams = [torch.cuda.Stream() for _ in systems]
+        ctxs = [Context(s, PREC_MIXED, stream=st.cuda_stream) for s, st in zip(systems, streams)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        om, stats, rc = binding.solve_batch(ctxs, n_eig, block, max_sub, res_tol=TOL_MIXED)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        for c in ctxs:
+            c.close()
+        return t, om, stats, rc
+
+    for _ in range(max(1, args.warmup)):
+        run_batch()
+    tb, om, stats, rc = min((run_batch() for _ in range(args.steps)), key=lambda x: x[0])
+    # sequential baseline: the same solves, one system at a time on one stream
+    ctxs = [Context(s, PREC_MIXED) for s in systems]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = []
+    for c in ctxs:
+        c.build_tau()
+        seq.append(c.davidson(n_eig, block, max_sub, res_tol=TOL_MIXED)[0])
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    err = []
+    for i in range(min(4, len(systems))):
+        c = Context(systems[i], PREC_FP64)
+        c.build_tau()
+        ref, _ = c.davidson(n_eig, block, max_sub, res_tol=TOL_FP64)
+        c.close()
+        err.append(float(np.abs(om[i] - ref).max() / MEV))
+    print(json.dumps({"mode": "batch", "n_systems": len(systems), "batch_s": tb,
+                      "sequential_s": ts, "speedup": ts / tb,
+                      "grids": [s.n_grid for s in systems], "n_occ": [s.n_occ for s in systems],
+                      "status": rc, "iterations": [st.iterations for st in stats],
+                      "max_err_meV_vs_fp64_first4": err}), flush=True)
+
+
 def apply_only(args, inst, ctx, stream, binding):
     """Operator-only timing: one bse_apply_liouville on a block of random conduction vectors."""
     import numpy as np
@@ -195,7 +248,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     from synth import CONFIGS
     metric = "time_to_16_lowest_VEEs_1meV_vs_fp64_plain"
-    probe = CONFIGS[args.config]()
+    probe = CONFIGS[args.config if not args.batch else "tiny"]()
     n_g = 2 * probe.n_half - 1
     cfg_desc = {"workload": f"{args.config}: L={probe.L:g} bohr, {probe.n_grid}^3 grid, N_G={n_g}, "
                             f"N_occ={probe.n_occ}, N_pdep={probe.n_pdep}, 15% of pairs, {N_EIG} VEEs, "
@@ -246,6 +299,8 @@ def main():
 
     if args.apply_only:
         return apply_only(args, inst, ctx, stream, binding)
+    if args.batch:
+        return batch_mode(args, binding, Context, PREC_MIXED, PREC_FP64)
 
     for _ in range(args.warmup):
         om_mixed, st = step()

@@ -157,6 +157,17 @@ typedef struct {
 int bse_davidson(bse_ctx* ctx, const bse_davidson_opts* opts, double* omega_out,
                  void* vec_out, bse_davidson_stats* stats);
 
+/* Batched solves (library addition; the paper distributes one system over many GPUs,
+ * Section 3): for each of n independent contexts -- typically many small systems of
+ * uneven grid and orbital counts -- builds tau if needed and runs bse_davidson with the
+ * same options, all concurrently, one host thread per context. Contexts created on
+ * distinct CUDA streams run their kernels concurrently on the device; contexts sharing a
+ * stream serialise. omega_out: host [n][opts->n_eig]; stats (nullable): host [n];
+ * status_out (nullable): host [n] per-system status. Returns BSE_OK or the first
+ * failing status. */
+int bse_solve_batch(bse_ctx* const* ctxs, int n, const bse_davidson_opts* opts, double* omega_out,
+                    bse_davidson_stats* stats, int* status_out);
+
 /* ---- Learned Davidson preconditioner (library addition; the paper's Davidson of
  * Section 3 has no learned component). A per-element MLP 5 -> 64 -> 64 -> 1 rescales the
  * diagonal step: features f = (1/2|G|^2, eps_v, theta, d - theta, r_e sqrt(dim)/||r||),

@@ -27,7 +27,7 @@ EXPORTS = ["bse_create", "bse_build_tau", "bse_get_pairs", "bse_get_overlaps",
            "bse_apply_liouville", "bse_davidson", "bse_last_error", "bse_version",
            "bse_destroy", "bse_profile", "bse_profile_read", "bse_apply_liouville_static",
            "bse_precond_collect", "bse_precond_set_samples", "bse_precond_grad",
-           "bse_precond_train", "bse_precond_load"]
+           "bse_precond_train", "bse_precond_load", "bse_solve_batch"]
 NPARAM = 4619
 
 
@@ -96,6 +96,8 @@ def load(path: str = LIB_PATH):
     lib.bse_precond_grad.argtypes = [P, F, C.c_int, D, D]
     lib.bse_precond_train.argtypes = [C.POINTER(P), C.c_int, F, C.c_int, C.c_double, C.c_int, F, D]
     lib.bse_precond_load.argtypes = [P, F]
+    lib.bse_solve_batch.argtypes = [C.POINTER(P), C.c_int, C.POINTER(DavidsonOpts), C.POINTER(C.c_double),
+                                    C.POINTER(DavidsonStats), C.POINTER(C.c_int)]
     lib.bse_destroy.argtypes = [P]
     lib.bse_destroy.restype = None
     for name in EXPORTS:
@@ -283,6 +285,23 @@ def precond_train(contexts, init, epochs=40, lr=3e-3, act_bf16=True):
     if rc != BSE_OK:
         raise BseError(rc, lib.bse_last_error(contexts[0].h).decode())
     return out, hist
+
+
+def solve_batch(contexts, n_eig, block, max_sub, max_it=200, res_tol=1e-5, precond=0):
+    """tau build (if needed) + Davidson for many contexts concurrently; returns (omega [n, n_eig],
+    stats list, status list)."""
+    lib = load()
+    n = len(contexts)
+    hs = (C.c_void_p * n)(*[c.h.value for c in contexts])
+    opts = DavidsonOpts(n_eig=n_eig, block=block, max_sub=max_sub, max_it=max_it, res_tol=res_tol,
+                        precond=precond)
+    om = np.zeros((n, n_eig))
+    st = (DavidsonStats * n)()
+    rc = (C.c_int * n)()
+    lib.bse_solve_batch(hs, n, C.byref(opts), _dptr(om), st, rc)
+    stats = [Stats(s.iterations, s.n_apply, s.ms_total, s.ms_apply, s.res_max, s.precond_fallbacks)
+             for s in st]
+    return om, stats, list(rc)
 
 
 def precond_init(seed=0):

@@ -13,6 +13,7 @@
 #include <memory>
 #include <queue>
 #include <string>
+#include <thread>
 #include <vector>
 
 using namespace bse;
@@ -106,6 +107,8 @@ struct bse_ctx {
   int *bptr = nullptr, *bw = nullptr;
   int4* bp = nullptr;
   int n_rblocks = 0;
+  int k1d_sc = 0;            // K1d vectors per CTA chosen by the autotuner (0: not tuned yet)
+  bool autotune = true;
   int64_t n_pairs = 0, nnz = 0;
   void* tau = nullptr;
   // operator workspace
@@ -133,15 +136,17 @@ int cuda_fail(bse_ctx* c, cudaError_t e, const char* what) {
     if (_e != cudaSuccess) return cuda_fail(c, _e, #call);   \
   } while (0)
 
+// Device allocations are stream-ordered on the context stream, so independent contexts
+// (e.g. a batch of systems on separate streams) never wait on each other's allocations.
 template <typename T>
 int dalloc(bse_ctx* c, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), c->st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     char buf[256];
-    snprintf(buf, sizeof(buf), "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+    snprintf(buf, sizeof(buf), "device allocation of %zu bytes failed: %s", count * sizeof(T),
              cudaGetErrorString(e));
     c->err = buf;
     return BSE_ERR_OOM;
@@ -153,7 +158,7 @@ void dfree(bse_ctx* c, void* p) {
   if (!p) return;
   auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
   if (it != c->allocs.end()) c->allocs.erase(it);
-  cudaFree(p);
+  cudaFreeAsync(p, c->st);
 }
 struct Scope {
   bse_ctx* c; int id = -1; cudaEvent_t a = nullptr; double bytes, flops;
@@ -326,6 +331,38 @@ int ensure_workspace(bse_ctx* c, long n_vec) {
 }
 
 // ---------------------------------------------------------------------------------
+// K1d tile autotuner: at the first application, time every vectors-per-CTA choice that
+// fits shared memory on the real inputs (twice each, CUDA events on the context stream)
+// and keep the fastest. The choice only changes the tiling, never the summation order.
+// ---------------------------------------------------------------------------------
+template <typename T>
+int autotune_k1d(bse_ctx* c, int nv, long n3, const T* ga, const T* gh, T* gr, double sf) {
+  if (!c->autotune) { c->k1d_sc = k1d_vectors_per_cta<T>(c->n_occ); return BSE_OK; }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_sc = 0;
+  for (int sc : {8, 4, 2, 1}) {
+    if (!k1d_fits<T>(c->n_occ, sc)) continue;
+    float t = 0;
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(cudaEventRecord(e0, c->st));
+      CK(k1d_tiled<T>(nv, c->n_occ, n3, ga, (const T*)c->tau, c->bptr, c->bw, c->bp, c->n_rblocks,
+                      vloc_of<T>(c), gh, upsi_of<T>(c), sf, gr, sc, c->st));
+      CK(cudaEventRecord(e1, c->st));
+      CK(cudaEventSynchronize(e1));
+      CK(cudaEventElapsedTime(&t, e0, e1));
+    }
+    if (t < best) { best = t; best_sc = sc; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->k1d_sc = best_sc ? best_sc : k1d_vectors_per_cta<T>(c->n_occ);
+  return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------------
 // R = P_c (D + K1e - K1d) A   (Eqs. evp, d, k1e, k1d)
 // ---------------------------------------------------------------------------------
 template <typename T>
@@ -377,8 +414,10 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
                ((double)c->n_pairs + 2.0 * nf + 1.0 + nv + c->n_occ) * n3 * sz,
                (2.0 * nnz * nv + 5.0 * nf) * n3);
       if (k1d_vectors_per_cta<T>(c->n_occ) > 0 && n3 % 32 == 0) {
+        if (c->k1d_sc == 0) CA(autotune_k1d<T>(c, (int)nv, n3, (const T*)ga, (const T*)gh, (T*)gr, sf));
         CK(k1d_tiled<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->bptr, c->bw, c->bp,
-                        c->n_rblocks, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
+                        c->n_rblocks, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr,
+                        c->k1d_sc, c->st));
       } else {
         CK(k1d_combine<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->nbr_ptr, c->nbr_w, c->nbr_p,
                           vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
@@ -855,9 +894,9 @@ const char* bse_last_error(const bse_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 void bse_destroy(bse_ctx* ctx) {
   if (!ctx) return;
-  cudaStreamSynchronize(ctx->st);
-  for (void* p : ctx->allocs) cudaFree(p);
+  for (void* p : ctx->allocs) cudaFreeAsync(p, ctx->st);
   ctx->allocs.clear();
+  cudaStreamSynchronize(ctx->st);
   delete ctx;
 }
 
@@ -929,6 +968,7 @@ int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) 
     cudaMemGetInfo(&fr, &tot);
     size_t bud = std::min<size_t>((size_t)64 << 30, (size_t)(0.4 * (double)fr));
     if (const char* e = getenv("BSE_WORKSPACE_GB")) bud = (size_t)(atof(e) * (double)(1ull << 30));
+    if (const char* e = getenv("BSE_AUTOTUNE")) c->autotune = atoi(e) != 0;
     c->ws_budget = std::max<size_t>(bud, 1);
   }
   // device uploads
@@ -1068,6 +1108,35 @@ int bse_davidson(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, void
     if (f != BSE_OK) return f;
   }
   return r;
+}
+
+int bse_solve_batch(bse_ctx* const* ctxs, int n, const bse_davidson_opts* o, double* omega_out,
+                    bse_davidson_stats* stats, int* status_out) {
+  if (!ctxs || n < 1 || !o || !omega_out) return BSE_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return BSE_ERR_INVALID_ARG;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<int> rc(n, BSE_OK);
+  std::vector<std::thread> th;
+  th.reserve(n);
+  for (int i = 0; i < n; ++i) {
+    th.emplace_back([&, i] {
+      cudaSetDevice(dev);
+      bse_ctx* c = ctxs[i];
+      int r = BSE_OK;
+      if (!c->tau_ready) r = bse_build_tau(c, nullptr, nullptr);
+      if (r == BSE_OK) r = bse_davidson(c, o, omega_out + (size_t)i * o->n_eig, nullptr, stats ? stats + i : nullptr);
+      rc[i] = r;
+    });
+  }
+  for (auto& t : th) t.join();
+  int first = BSE_OK;
+  for (int i = 0; i < n; ++i) {
+    if (status_out) status_out[i] = rc[i];
+    if (first == BSE_OK && rc[i] != BSE_OK) first = rc[i];
+  }
+  return first;
 }
 
 int bse_profile(bse_ctx* c, int mode) {
@@ -1433,7 +1502,8 @@ int apply_static_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out, unsigned 
   if (nf & 1) CK(cudaMemsetAsync(gr + (ngr - 1) * n3, 0, (size_t)n3 * sizeof(cplx<T>), c->st));
   if (k1d_vectors_per_cta<T>(c->n_occ) > 0 && n3 % 32 == 0) {
     CK(k1d_tiled<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, c->bptr, c->bw, c->bp,
-                    c->n_rblocks, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
+                    c->n_rblocks, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->k1d_sc,
+                    c->st));
   } else {
     CK(k1d_combine<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, c->nbr_ptr, c->nbr_w,
                       c->nbr_p, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));

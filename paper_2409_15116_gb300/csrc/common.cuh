@@ -3,6 +3,15 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
+#include <mutex>
+
+// Runs a one-time set-up call (e.g. a kernel attribute) once per process, thread-safe;
+// every caller gets the status of that one call.
+template <typename F>
+inline cudaError_t once_status(std::once_flag& flag, cudaError_t& status, F&& fn) {
+  std::call_once(flag, [&] { status = fn(); });
+  return status;
+}
 
 template <typename T> struct cplx_of;
 template <> struct cplx_of<float> { using type = float2; };

@@ -238,14 +238,13 @@ cudaError_t eigh_lowest(int m, int k, const double* A, long lda, double* work, d
   if (m <= 0 || k <= 0) return cudaSuccess;
   if (m > EIGH_MAX || k > EIGH_KMAX || k > m) return cudaErrorInvalidValue;
   const size_t smem = ((size_t)m * (m + 1) + 4 * (size_t)m + EIGH_KMAX) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag once;
+  static cudaError_t once_st = cudaSuccess;
+  cudaError_t e0 = once_status(once, once_st, [&] {
     const size_t mx = ((size_t)EIGH_MAX * (EIGH_MAX + 1) + 4 * EIGH_MAX + EIGH_KMAX) * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(eigh_lowest_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+    return cudaFuncSetAttribute(eigh_lowest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+  });
+  if (e0 != cudaSuccess) return e0;
   double* Z = work;                       // m x k, column-major
   double* scratch = work + (size_t)m * k; // 3 m per vector
   eigh_lowest_kernel<<<1, 512, smem, st>>>(m, k, A, lda, Z, scratch, V, w, info);

@@ -161,13 +161,12 @@ static cudaError_t launch_fft3d(cplx<T>* data, long n_batch, int sign, const cpl
                                 cudaStream_t st) {
   constexpr int TX = Plan<N>::TX;
   const size_t smem = (size_t)(2 * TX * Pad<N>::LS + N) * sizeof(cplx<T>);
-  static bool attr_set = false;   // per instantiation; attribute is per device function
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(fft_axis_kernel<T, N>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::once_flag once;
+  static cudaError_t once_st = cudaSuccess;
+  cudaError_t e0 = once_status(once, once_st, [&] {
+    return cudaFuncSetAttribute(fft_axis_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e0 != cudaSuccess) return e0;
   const long blocks = n_batch * (long)N * N / TX;
   if (blocks <= 0) return cudaSuccess;
   for (int axis = 0; axis < 3; ++axis) {

@@ -146,13 +146,12 @@ static cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T
                               const T* vloc, const T* vh, const T* upsi, double sf, T* out,
                               cudaStream_t st) {
   const size_t smem = ((size_t)n_occ * SC * TR + SC * TR) * sizeof(T);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k1d_tile_kernel<T, TR, SC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::once_flag once;
+  static cudaError_t once_st = cudaSuccess;
+  cudaError_t e0 = once_status(once, once_st, [&] {
+    return cudaFuncSetAttribute(k1d_tile_kernel<T, TR, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  if (e0 != cudaSuccess) return e0;
   const long tiles = n3 / TR;
   const long blocks = tiles * ((n_vec + SC - 1) / SC);
   k1d_tile_kernel<T, TR, SC><<<(unsigned)blocks, 256, smem, st>>>(
@@ -181,14 +180,24 @@ int k1d_vectors_per_cta(int n_occ) {
   return 0;
 }
 
+// whether SC vectors per CTA fit the 200 KB opt-in shared memory
+template <typename T>
+bool k1d_fits(int n_occ, int sc) {
+  constexpr int TR = BSE_K1D_TR;
+  return (size_t)n_occ * sc * TR * sizeof(T) + sc * TR * sizeof(T) <= 200 * 1024;
+}
+
+// sc: vectors per CTA (8, 4, 2 or 1; 0 picks the largest within the default budget)
 template <typename T>
 cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, const int* bptr,
                       const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
-                      const T* upsi, double sf, T* out, cudaStream_t st) {
+                      const T* upsi, double sf, T* out, int sc, cudaStream_t st) {
   constexpr int TR = BSE_K1D_TR;
   if (n_vec <= 0) return cudaSuccess;
   if (n3 % TR) return cudaErrorInvalidValue;
-  switch (k1d_vectors_per_cta<T>(n_occ)) {
+  if (sc == 0) sc = k1d_vectors_per_cta<T>(n_occ);
+  if (!k1d_fits<T>(n_occ, sc)) return cudaErrorInvalidValue;
+  switch (sc) {
     case 8: return launch_k1d<T, TR, 8>(n_vec, n_occ, n3, a, tau, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, out, st);
     case 4: return launch_k1d<T, TR, 4>(n_vec, n_occ, n3, a, tau, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, out, st);
     case 2: return launch_k1d<T, TR, 2>(n_vec, n_occ, n3, a, tau, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, out, st);
@@ -197,8 +206,10 @@ cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, c
   }
 }
 
-template cudaError_t k1d_tiled<float>(int, int, long, const float*, const float*, const int*, const int*, const int4*, int, const float*, const float*, const float*, double, float*, cudaStream_t);
-template cudaError_t k1d_tiled<double>(int, int, long, const double*, const double*, const int*, const int*, const int4*, int, const double*, const double*, const double*, double, double*, cudaStream_t);
+template cudaError_t k1d_tiled<float>(int, int, long, const float*, const float*, const int*, const int*, const int4*, int, const float*, const float*, const float*, double, float*, int, cudaStream_t);
+template cudaError_t k1d_tiled<double>(int, int, long, const double*, const double*, const int*, const int*, const int4*, int, const double*, const double*, const double*, double, double*, int, cudaStream_t);
+template bool k1d_fits<float>(int, int);
+template bool k1d_fits<double>(int, int);
 template int k1d_vectors_per_cta<float>(int);
 template int k1d_vectors_per_cta<double>(int);
 

@@ -91,9 +91,11 @@ cudaError_t row_dots(int ns, long dim, const double* A, const double* B, double*
 template <typename T>
 int k1d_vectors_per_cta(int n_occ);
 template <typename T>
+bool k1d_fits(int n_occ, int sc);
+template <typename T>
 cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, const int* bptr,
                       const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
-                      const T* upsi, double sf, T* out, cudaStream_t st);
+                      const T* upsi, double sf, T* out, int sc, cudaStream_t st);
 template <typename T>
 cudaError_t scale_columns(int rows, int cols, T* C, long ldc, const double* f, cudaStream_t st);
 template <typename TI, typename TO>

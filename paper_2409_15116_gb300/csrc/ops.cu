@@ -438,13 +438,13 @@ cudaError_t cholesky_inverse(int b, const double* S, long lds, double* Linv, int
   if (b <= 0) return cudaSuccess;
   if (b > CHOL_MAX) return cudaErrorInvalidValue;
   const size_t smem = (size_t)b * (b + 1) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((size_t)CHOL_MAX * (CHOL_MAX + 1) * 8));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::once_flag once;
+  static cudaError_t once_st = cudaSuccess;
+  cudaError_t e0 = once_status(once, once_st, [&] {
+    return cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((size_t)CHOL_MAX * (CHOL_MAX + 1) * 8));
+  });
+  if (e0 != cudaSuccess) return e0;
   cholesky_kernel<<<1, 256, smem, st>>>(b, S, lds, Linv, info); note_launch();
   return cudaGetLastError();
 }

@@ -196,14 +196,15 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_bf16x3_kernel(
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 static bool get_encoder() {
-  if (g_encode) return true;
-  void* fn = nullptr;
-  cudaDriverEntryPointQueryResult q;
-  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-      q != cudaDriverEntryPointSuccess || !fn)
-    return false;
-  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  return true;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess && fn)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  return g_encode != nullptr;
 }
 
 // 2-D bf16 tensor map over [rows x cols] with row stride ld (elements), box 64 x 128, 128B swizzle
@@ -227,12 +228,12 @@ cudaError_t tc_gemm_bf16x3(const void* mAh, const void* mAl, const void* mBh, co
                            int K, double alpha, double beta, float* out, long ldo, int splits, int* err,
                            cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::once_flag once;
+  static cudaError_t once_st = cudaSuccess;
+  cudaError_t e0 = once_status(once, once_st, [&] {
+    return cudaFuncSetAttribute(tc_gemm_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  });
+  if (e0 != cudaSuccess) return e0;
   const int kt_all = (K + TC_BK - 1) / TC_BK;
   if (splits < 1) splits = 1;
   if (splits > kt_all) splits = kt_all > 0 ? kt_all : 1;
