@@ -107,7 +107,7 @@ struct bse_ctx {
   int *bptr = nullptr, *bw = nullptr;
   int4* bp = nullptr;
   int n_rblocks = 0;
-  int k1d_sc = 0;            // K1d vectors per CTA chosen by the autotuner (0: not tuned yet)
+  int k1d_sc = 0;            // K1d tile variant chosen by the autotuner (0: not tuned yet)
   bool autotune = true;
   int64_t n_pairs = 0, nnz = 0;
   void* tau = nullptr;
@@ -331,24 +331,25 @@ int ensure_workspace(bse_ctx* c, long n_vec) {
 }
 
 // ---------------------------------------------------------------------------------
-// K1d tile autotuner: at the first application, time every vectors-per-CTA choice that
-// fits shared memory on the real inputs (twice each, CUDA events on the context stream)
-// and keep the fastest. The choice only changes the tiling, never the summation order.
+// K1d tile autotuner: at the first application, time every tile variant (points and
+// vectors per CTA) that fits shared memory on the real inputs (twice each, CUDA events on
+// the context stream) and keep the fastest. The choice only changes the tiling, never
+// the summation order.
 // ---------------------------------------------------------------------------------
 template <typename T>
 int autotune_k1d(bse_ctx* c, int nv, long n3, const T* ga, const T* gh, T* gr, double sf) {
-  if (!c->autotune) { c->k1d_sc = k1d_vectors_per_cta<T>(c->n_occ); return BSE_OK; }
+  if (!c->autotune) { c->k1d_sc = k1d_default_variant<T>(c->n_occ); return BSE_OK; }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_sc = 0;
-  for (int sc : {8, 4, 2, 1}) {
+  for (int sc = 1; sc <= k1d_num_variants(); ++sc) {
     if (!k1d_fits<T>(c->n_occ, sc)) continue;
     float t = 0;
     for (int rep = 0; rep < 2; ++rep) {
       CK(cudaEventRecord(e0, c->st));
-      CK(k1d_tiled<T>(nv, c->n_occ, n3, ga, (const T*)c->tau, c->bptr, c->bw, c->bp, c->n_rblocks,
+      CK(k1d_tiled<T>(nv, c->n_occ, n3, ga, (const T*)c->tau, c->n_pairs, c->bptr, c->bw, c->bp, c->n_rblocks,
                       vloc_of<T>(c), gh, upsi_of<T>(c), sf, gr, sc, c->st));
       CK(cudaEventRecord(e1, c->st));
       CK(cudaEventSynchronize(e1));
@@ -358,7 +359,7 @@ int autotune_k1d(bse_ctx* c, int nv, long n3, const T* ga, const T* gh, T* gr, d
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c->k1d_sc = best_sc ? best_sc : k1d_vectors_per_cta<T>(c->n_occ);
+  c->k1d_sc = best_sc ? best_sc : k1d_default_variant<T>(c->n_occ);
   return BSE_OK;
 }
 
@@ -413,13 +414,13 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
       Scope sc(c, "k1d_combine",
                ((double)c->n_pairs + 2.0 * nf + 1.0 + nv + c->n_occ) * n3 * sz,
                (2.0 * nnz * nv + 5.0 * nf) * n3);
-      if (k1d_vectors_per_cta<T>(c->n_occ) > 0 && n3 % 32 == 0) {
+      if (k1d_default_variant<T>(c->n_occ) > 0 && n3 % 16 == 0) {
         if (c->k1d_sc == 0) CA(autotune_k1d<T>(c, (int)nv, n3, (const T*)ga, (const T*)gh, (T*)gr, sf));
-        CK(k1d_tiled<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->bptr, c->bw, c->bp,
+        CK(k1d_tiled<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->n_pairs, c->bptr, c->bw, c->bp,
                         c->n_rblocks, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr,
                         c->k1d_sc, c->st));
       } else {
-        CK(k1d_combine<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->nbr_ptr, c->nbr_w, c->nbr_p,
+        CK(k1d_combine<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->n_pairs, c->nbr_ptr, c->nbr_w, c->nbr_p,
                           vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
       }
     }
@@ -568,7 +569,7 @@ int build_tau_impl(bse_ctx* c) {
     }
     CK(grid_coulomb<T>(grids, ng, c->N, c->L, c->omega, 1, 1.0, c->st));
     CK(fft3d<T>(grids, ng, c->N, +1, tw_of<T>(c), c->st));
-    CK(deinterleave_pairs<T>(b, grids, n3, tau + p0 * n3, c->st));
+    CK(deinterleave_pairs<T>(b, grids, n3, p0, c->n_pairs, tau, c->st));
   }
   CK(cudaStreamSynchronize(c->st));
   dfree(c, grids); dfree(c, X); dfree(c, X2); dfree(c, Cp);
@@ -969,6 +970,12 @@ int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) 
     size_t bud = std::min<size_t>((size_t)64 << 30, (size_t)(0.4 * (double)fr));
     if (const char* e = getenv("BSE_WORKSPACE_GB")) bud = (size_t)(atof(e) * (double)(1ull << 30));
     if (const char* e = getenv("BSE_AUTOTUNE")) c->autotune = atoi(e) != 0;
+    // BSE_K1D_VARIANT=v fixes the K1d tile variant (no autotuning); ignored if it does not fit
+    if (const char* e = getenv("BSE_K1D_VARIANT")) {
+      const int v = atoi(e);
+      const bool ok = (precision == BSE_PREC_FP64) ? k1d_fits<double>(s->n_occ, v) : k1d_fits<float>(s->n_occ, v);
+      if (ok) c->k1d_sc = v;
+    }
     c->ws_budget = std::max<size_t>(bud, 1);
   }
   // device uploads
@@ -1500,12 +1507,12 @@ int apply_static_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out, unsigned 
     CK(fft3d<T>(gh, nh, N, +1, tw_of<T>(c), c->st));
   }
   if (nf & 1) CK(cudaMemsetAsync(gr + (ngr - 1) * n3, 0, (size_t)n3 * sizeof(cplx<T>), c->st));
-  if (k1d_vectors_per_cta<T>(c->n_occ) > 0 && n3 % 32 == 0) {
-    CK(k1d_tiled<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, c->bptr, c->bw, c->bp,
+  if (k1d_default_variant<T>(c->n_occ) > 0 && n3 % 16 == 0) {
+    CK(k1d_tiled<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, c->n_pairs, c->bptr, c->bw, c->bp,
                     c->n_rblocks, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->k1d_sc,
                     c->st));
   } else {
-    CK(k1d_combine<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, c->nbr_ptr, c->nbr_w,
+    CK(k1d_combine<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, c->n_pairs, c->nbr_ptr, c->nbr_w,
                       c->nbr_p, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
   }
   CK(fft3d<T>(gr, ngr, N, -1, tw_of<T>(c), c->st));

@@ -40,6 +40,14 @@ __device__ __forceinline__ size_t pair_off(long f, long r, long n3) {
   return (size_t)(f >> 1) * 2 * (size_t)n3 + 2 * (size_t)r + (size_t)(f & 1);
 }
 
+// tau_p(r) for n_pairs pairs is stored point-tiled: tiles of TAU_TB consecutive grid
+// points, each holding all pairs' values at those points, [n3/TAU_TB][n_pairs][TAU_TB].
+// A CTA that works on a few points reads one contiguous stretch of tau.
+constexpr int TAU_TB = 16;
+__host__ __device__ __forceinline__ size_t tau_off(long p, long r, long n_pairs) {
+  return ((size_t)(r / TAU_TB) * (size_t)n_pairs + (size_t)p) * TAU_TB + (size_t)(r % TAU_TB);
+}
+
 namespace bse {
 // count of kernel launches issued by this library (host side, all contexts)
 void note_launch();

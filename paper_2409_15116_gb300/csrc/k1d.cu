@@ -4,213 +4,303 @@
 //   u_R,sv(r) = V_loc(r) u_a,sv(r) + s V_H,s(r) u_psi,v(r) - sum_{w in nbr(v)} tau_vw(r) u_a,sw(r)
 //
 // At each grid point the sum is a sparse (N_occ x N_occ) times dense (N_occ x n_vec)
-// product whose sparse factor tau(r) changes from point to point. A CTA owns a tile of
-// TR consecutive points and a chunk of SC trial vectors: it stages a(r) for every orbital
-// of the chunk in shared memory (read from HBM once, 128-byte rows), then streams tau
-// through rows grouped four at a time (one localisation site): each tau value is
-// loaded once per tile and reused for the SC vectors, each staged a value feeds the
-// four rows of a block. tau_vw(r) for pairs outside the overlap list is simply absent
-// (Eq. overlap); blocks list the union of their rows' neighbours with -1 for the
-// missing entries.
+// product whose sparse factor tau(r) changes from point to point, so no operand is shared
+// across points and the work is SIMT multiply-adds fed from memory. A CTA owns a tile of
+// TR consecutive points and a chunk of SC trial vectors:
+//
+//  * a(r) for every orbital of the chunk is copied into shared memory with cp.async
+//    (no registers held, all copies in flight at once), laid out [w][t][s] so that a lane
+//    reads the SC values it needs for orbital w as one or two 16-byte loads;
+//  * groups of TR lanes (one lane per point) walk row blocks of four orbitals (one
+//    localisation site); each block lists the union of its rows' neighbours w, with the
+//    four pair indices (-1 where a row has no such neighbour, Eq. overlap);
+//  * tau values go straight from global memory to registers through a ring of PD entries,
+//    so PD entries of loads are in flight per lane while the oldest one is consumed; tau is
+//    stored point-tiled, so the tau a CTA reads is one contiguous stretch of memory;
+//  * each tau value feeds SC multiply-adds and each staged a value four, accumulated in
+//    packed FP32x2 FMAs for single precision.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace bse {
 
-template <typename T, int TR, int SC>
-__global__ void __launch_bounds__(256, 3) k1d_tile_kernel(
-    int n_vec, int n_occ, long n3, const T* __restrict__ a, const T* __restrict__ tau,
-    const int* __restrict__ bptr, const int* __restrict__ bw, const int4* __restrict__ bp,
-    int n_blocks, const T* __restrict__ vloc, const T* __restrict__ vh,
-    const T* __restrict__ upsi, T sf, T* __restrict__ out) {
-  using C = cplx<T>;
-  extern __shared__ __align__(16) unsigned char k1d_smem[];
-  T* A = reinterpret_cast<T*>(k1d_smem);            // [n_occ][SC][TR]
-  T* VH = A + (size_t)n_occ * SC * TR;               // [SC][TR]
-  const int n_sc = (n_vec + SC - 1) / SC;
-  const int sc = blockIdx.x % n_sc;
-  const long tile = blockIdx.x / n_sc;
-  const long r0 = tile * TR;
-  const int s0 = sc * SC;
-  const int ns = min(SC, n_vec - s0);
-  const int tid = threadIdx.x;
-  // stage a(f, r0 .. r0+TR) for the fields f of this vector chunk
-  const long f_lo = (long)s0 * n_occ, f_hi = (long)(s0 + ns) * n_occ;
-  const long c_lo = f_lo >> 1, c_hi = (f_hi + 1) >> 1;
-  const C* ac = reinterpret_cast<const C*>(a);
-  if ((n_occ & 1) == 0) {
-    // even N_occ: complex grid c holds orbitals (2k, 2k+1) of one vector; a warp moves
-    // two 128-byte rows (16 complex values each) per iteration, no per-element division
-    const int half = n_occ >> 1;
-    const int rows = ns * half;
-    const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    const int sub = lane / TR, t = lane % TR;        // TR divides 32
-    constexpr int RPW = 32 / TR;                     // rows per warp pass
-    for (int row = wid * RPW + sub; row < rows; row += nw * RPW) {
-      const int sl = row / half, k = row - sl * half;
-      const C z = ac[(c_lo + row) * n3 + r0 + t];
-      A[((2 * k) * SC + sl) * TR + t] = z.x;
-      A[((2 * k + 1) * SC + sl) * TR + t] = z.y;
-    }
+namespace {
+
+constexpr int K1D_THREADS = 256;
+constexpr int K1D_PD = 8;                       // tau prefetch depth (entries per lane)
+constexpr size_t K1D_SMEM_MAX = 220 * 1024;     // opt-in dynamic shared memory used at most
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (BYTES == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// SC consecutive values from shared memory in 16-, 8- or 4-byte loads
+template <typename T, int SC>
+__device__ __forceinline__ void lds_vec(T (&v)[SC], const T* p) {
+  constexpr int B = SC * (int)sizeof(T);
+  if constexpr (B % 16 == 0) {
+#pragma unroll
+    for (int k = 0; k < B / 16; ++k) reinterpret_cast<uint4*>(v)[k] = reinterpret_cast<const uint4*>(p)[k];
+  } else if constexpr (B == 8) {
+    *reinterpret_cast<uint2*>(v) = *reinterpret_cast<const uint2*>(p);
   } else {
-    for (long e = tid; e < (c_hi - c_lo) * TR; e += blockDim.x) {
-      const long c = c_lo + e / TR;
-      const int t = (int)(e % TR);
-      const C z = ac[c * n3 + r0 + t];
-      const long f0 = 2 * c, f1 = f0 + 1;
-      if (f0 >= f_lo) {
-        const long q = f0 - f_lo;
-        A[((q % n_occ) * SC + q / n_occ) * TR + t] = z.x;
-      }
-      if (f1 < f_hi) {
-        const long q = f1 - f_lo;
-        A[((q % n_occ) * SC + q / n_occ) * TR + t] = z.y;
-      }
-    }
+    v[0] = p[0];
   }
-  for (int e = tid; e < SC * TR; e += blockDim.x) {
-    const int s = e / TR, t = e % TR;
-    VH[e] = (s < ns) ? vh[pair_off<T>(s0 + s, r0 + t, n3)] : (T)0;
-  }
-  __syncthreads();
-  const int t = tid % TR, g = tid / TR, G = blockDim.x / TR;
-  const long r = r0 + t;
-  const T vl = vloc[r];
-  for (int rb = g; rb < n_blocks; rb += G) {
-    T acc[4][SC];
+}
+
+// accumulators of one lane: four rows x SC vectors
+template <typename T, int SC, bool PACKED = (sizeof(T) == 4 && SC % 2 == 0)>
+struct RowAcc {
+  T acc[4][SC];
+  __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int s = 0; s < SC; ++s) acc[i][s] = (T)0;
-    const int e0 = bptr[rb], e1 = bptr[rb + 1];
-    // two-deep software pipeline on the tau loads (entries e+1 and e+2 in flight)
-    T tq[2][4];
-    int wq[2];
+  }
+  __device__ __forceinline__ void mac(const T (&tv)[4], const T* Aw) {
+    T av[SC];
+    lds_vec<T, SC>(av, Aw);
 #pragma unroll
-    for (int d = 0; d < 2; ++d) {
-      const int e = e0 + d;
-      wq[d] = 0;
-      tq[d][0] = tq[d][1] = tq[d][2] = tq[d][3] = (T)0;
-      if (e < e1) {
-        const int4 p = bp[e];
-        wq[d] = bw[e];
-        tq[d][0] = p.x >= 0 ? tau[(long)p.x * n3 + r] : (T)0;
-        tq[d][1] = p.y >= 0 ? tau[(long)p.y * n3 + r] : (T)0;
-        tq[d][2] = p.z >= 0 ? tau[(long)p.z * n3 + r] : (T)0;
-        tq[d][3] = p.w >= 0 ? tau[(long)p.w * n3 + r] : (T)0;
-      }
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int s = 0; s < SC; ++s) acc[i][s] = fma(tv[i], av[s], acc[i][s]);
+  }
+  __device__ __forceinline__ T get(int i, int s) const { return acc[i][s]; }
+};
+
+template <int SC>
+struct RowAcc<float, SC, true> {
+  float2 acc[4][SC / 2];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < SC / 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ void mac(const float (&tv)[4], const float* Aw) {
+    float av[SC];
+    lds_vec<float, SC>(av, Aw);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 ti = make_float2(tv[i], tv[i]);
+#pragma unroll
+      for (int j = 0; j < SC / 2; ++j)
+        acc[i][j] = __ffma2_rn(ti, make_float2(av[2 * j], av[2 * j + 1]), acc[i][j]);
     }
-    for (int e = e0; e < e1; ++e) {
-      const int w = wq[0];
-      const T t0 = tq[0][0], t1 = tq[0][1], t2 = tq[0][2], t3 = tq[0][3];
-      wq[0] = wq[1];
+  }
+  __device__ __forceinline__ float get(int i, int s) const { return (s & 1) ? acc[i][s >> 1].y : acc[i][s >> 1].x; }
+};
+
+// group-wide broadcast of lane j's value (lanes of a group = TR consecutive lanes)
+template <int TR>
+__device__ __forceinline__ int gshfl(unsigned mask, int v, int j) { return __shfl_sync(mask, v, j, TR); }
+
+template <typename T, int TR, int SC>
+__global__ void __launch_bounds__(K1D_THREADS, 2) k1d_tile_kernel(
+    int n_vec, int n_occ, long n3, const T* __restrict__ a, const T* __restrict__ tau, long n_pairs,
+    const int* __restrict__ bptr, const int* __restrict__ bw, const int4* __restrict__ bp,
+    int n_blocks, const T* __restrict__ vloc, const T* __restrict__ vh,
+    const T* __restrict__ upsi, T sf, T* __restrict__ out) {
+  // ring depth (divides TR); half as deep in double precision, whose values take two registers
+  constexpr int PD0 = (sizeof(T) == 8) ? K1D_PD / 2 : K1D_PD;
+  constexpr int PD = (PD0 < TR) ? PD0 : TR;
+  extern __shared__ __align__(16) unsigned char k1d_smem[];
+  T* A = reinterpret_cast<T*>(k1d_smem);            // [n_occ][TR][SC]
+  T* VH = A + (size_t)n_occ * TR * SC;               // [TR][SC]
+  const int n_sc = (n_vec + SC - 1) / SC;
+  const int chunk = blockIdx.x % n_sc;
+  const long r0 = (long)(blockIdx.x / n_sc) * TR;
+  const int s0 = chunk * SC;
+  const int ns = min(SC, n_vec - s0);
+  const int tid = threadIdx.x;
+  const int t = tid % TR, g = tid / TR;
+  constexpr int G = K1D_THREADS / TR;
+  const long r = r0 + t;
+  // stage a(field (s0+s, w), r0+t) -> A[w][t][s]: item (w, t, s) with s fastest, so the
+  // lanes of a warp fill consecutive shared-memory words
+  {
+    const int n_items = n_occ * TR * SC;
+    for (int it = tid; it < n_items; it += K1D_THREADS) {
+      const int s = it % SC, tt = (it / SC) % TR, w = it / (SC * TR);
+      if (s < ns)
+        cp_async<sizeof(T)>(A + it, a + pair_off<T>((long)(s0 + s) * n_occ + w, r0 + tt, n3));
+    }
+  }
+  if (g < SC) VH[t * SC + g] = (g < ns) ? vh[pair_off<T>(s0 + g, r, n3)] : (T)0;
+  cp_async_wait_all();
+  __syncthreads();
+  const T vl = vloc[r];
+  const T* tau_r = tau + tau_off(0, r, n_pairs);     // pair p at tau_r[p * TAU_TB]
+  const unsigned gmask = (TR == 32) ? 0xffffffffu : (((1u << TR) - 1u) << ((tid & 31) & ~(TR - 1)));
+  for (int rb = g; rb < n_blocks; rb += G) {
+    RowAcc<T, SC> acc;
+    acc.zero();
+    const int e0 = bptr[rb], e1 = bptr[rb + 1];
+    // block-entry indices in batches of TR: lane t of the group holds entry base + t.
+    // Three batches are live (current, next, the one after), so an index load has more
+    // than a batch of work to arrive before its tau loads are issued.
+    auto ld_idx = [&](int base, int4& p, int& w) {
+      const int e = base + t;
+      if (e < e1) { p = bp[e]; w = bw[e]; } else { p = make_int4(-1, -1, -1, -1); w = 0; }
+    };
+    int4 pA, pB, pC;
+    int wA, wB, wC;
+    ld_idx(e0, pA, wA);
+    ld_idx(e0 + TR, pB, wB);
+    // ring of PD entries in flight: slot d holds tau (four rows) and the neighbour w
+    T tq[PD][4];
+    int wq[PD];
+    auto issue = [&](int px, int py, int pz, int pw, T (&tv)[4]) {
+      tv[0] = (px >= 0) ? tau_r[(size_t)px * TAU_TB] : (T)0;
+      tv[1] = (py >= 0) ? tau_r[(size_t)py * TAU_TB] : (T)0;
+      tv[2] = (pz >= 0) ? tau_r[(size_t)pz * TAU_TB] : (T)0;
+      tv[3] = (pw >= 0) ? tau_r[(size_t)pw * TAU_TB] : (T)0;
+    };
 #pragma unroll
-      for (int i = 0; i < 4; ++i) tq[0][i] = tq[1][i];
-      if (e + 2 < e1) {
-        const int4 p = bp[e + 2];
-        wq[1] = bw[e + 2];
-        tq[1][0] = p.x >= 0 ? tau[(long)p.x * n3 + r] : (T)0;
-        tq[1][1] = p.y >= 0 ? tau[(long)p.y * n3 + r] : (T)0;
-        tq[1][2] = p.z >= 0 ? tau[(long)p.z * n3 + r] : (T)0;
-        tq[1][3] = p.w >= 0 ? tau[(long)p.w * n3 + r] : (T)0;
-      }
-      const T* Aw = A + (size_t)w * SC * TR + t;
+    for (int d = 0; d < PD; ++d) {
+      const int px = gshfl<TR>(gmask, pA.x, d), py = gshfl<TR>(gmask, pA.y, d);
+      const int pz = gshfl<TR>(gmask, pA.z, d), pw = gshfl<TR>(gmask, pA.w, d);
+      wq[d] = gshfl<TR>(gmask, wA, d);
+      issue(px, py, pz, pw, tq[d]);
+    }
+    for (int base = e0; base < e1; base += TR) {
+      ld_idx(base + 2 * TR, pC, wC);
 #pragma unroll
-      for (int s = 0; s < SC; ++s) {
-        const T av = Aw[s * TR];
-        acc[0][s] = fma(t0, av, acc[0][s]);
-        acc[1][s] = fma(t1, av, acc[1][s]);
-        acc[2][s] = fma(t2, av, acc[2][s]);
-        acc[3][s] = fma(t3, av, acc[3][s]);
+      for (int d = 0; d < TR; ++d) {
+        if (base + d >= e1) break;
+        const int sl = d % PD;
+        acc.mac(tq[sl], A + ((size_t)wq[sl] * TR + t) * SC);
+        // refill the slot with entry base + d + PD (index from batch A or B)
+        const int j = d + PD;
+        int px, py, pz, pw, w;
+        if (j < TR) {
+          px = gshfl<TR>(gmask, pA.x, j); py = gshfl<TR>(gmask, pA.y, j);
+          pz = gshfl<TR>(gmask, pA.z, j); pw = gshfl<TR>(gmask, pA.w, j);
+          w = gshfl<TR>(gmask, wA, j);
+        } else {
+          px = gshfl<TR>(gmask, pB.x, j - TR); py = gshfl<TR>(gmask, pB.y, j - TR);
+          pz = gshfl<TR>(gmask, pB.z, j - TR); pw = gshfl<TR>(gmask, pB.w, j - TR);
+          w = gshfl<TR>(gmask, wB, j - TR);
+        }
+        wq[sl] = w;
+        issue(px, py, pz, pw, tq[sl]);
       }
+      pA = pB; wA = wB;
+      pB = pC; wB = wC;
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int v = 4 * rb + i;
       if (v >= n_occ) break;
-      const T up = upsi[pair_off<T>(v, r, n3)];
-      const T* Av = A + (size_t)v * SC * TR + t;
+      const T up = sf * upsi[pair_off<T>(v, r, n3)];
+      T av[SC], hv[SC];
+      lds_vec<T, SC>(av, A + ((size_t)v * TR + t) * SC);
+      lds_vec<T, SC>(hv, VH + t * SC);
 #pragma unroll
       for (int s = 0; s < SC; ++s) {
         if (s >= ns) break;
         const long f = (long)(s0 + s) * n_occ + v;
-        out[pair_off<T>(f, r, n3)] = vl * Av[s * TR] + sf * VH[s * TR + t] * up - acc[i][s];
+        out[pair_off<T>(f, r, n3)] = vl * av[s] + hv[s] * up - acc.get(i, s);
       }
     }
   }
 }
 
+// tile variants: (points per CTA, vectors per CTA)
+struct Variant { int tr, sc; };
+constexpr Variant kVariants[] = {{0, 0}, {16, 8}, {8, 8}, {16, 4}, {8, 4}, {16, 2}, {16, 1}};
+constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0])) - 1;
+
+template <typename T>
+size_t variant_smem(int n_occ, int v) {
+  const Variant q = kVariants[v];
+  return ((size_t)n_occ * q.tr * q.sc + (size_t)q.tr * q.sc) * sizeof(T);
+}
+
 template <typename T, int TR, int SC>
-static cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T* tau,
-                              const int* bptr, const int* bw, const int4* bp, int n_blocks,
-                              const T* vloc, const T* vh, const T* upsi, double sf, T* out,
-                              cudaStream_t st) {
-  const size_t smem = ((size_t)n_occ * SC * TR + SC * TR) * sizeof(T);
-  static std::once_flag once;
-  static cudaError_t once_st = cudaSuccess;
-  cudaError_t e0 = once_status(once, once_st, [&] {
-    return cudaFuncSetAttribute(k1d_tile_kernel<T, TR, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  });
-  if (e0 != cudaSuccess) return e0;
-  const long tiles = n3 / TR;
-  const long blocks = tiles * ((n_vec + SC - 1) / SC);
-  k1d_tile_kernel<T, TR, SC><<<(unsigned)blocks, 256, smem, st>>>(
-      n_vec, n_occ, n3, a, tau, bptr, bw, bp, n_blocks, vloc, vh, upsi, (T)sf, out);
-  note_launch();
-  return cudaGetLastError();
-}
-
-// shared-memory budget of the a(r) stage; SC (vectors per CTA) is the largest power of
-// two with n_occ * SC * TR * sizeof(T) within it. A budget near 72 KB lets three CTAs
-// (24 warps) share an SM, which the tau loads need for latency hiding.
-#ifndef BSE_K1D_SMEM_KB
-#define BSE_K1D_SMEM_KB 72
-#endif
-constexpr size_t K1D_SMEM_BUDGET = (size_t)BSE_K1D_SMEM_KB * 1024;
-
-#ifndef BSE_K1D_TR
-#define BSE_K1D_TR 16
-#endif
-
-template <typename T>
-int k1d_vectors_per_cta(int n_occ) {
-  constexpr int TR = BSE_K1D_TR;
-  for (int sc = 8; sc >= 1; sc >>= 1)
-    if ((size_t)n_occ * sc * TR * sizeof(T) + sc * TR * sizeof(T) <= K1D_SMEM_BUDGET) return sc;
-  return 0;
-}
-
-// whether SC vectors per CTA fit the 200 KB opt-in shared memory
-template <typename T>
-bool k1d_fits(int n_occ, int sc) {
-  constexpr int TR = BSE_K1D_TR;
-  return (size_t)n_occ * sc * TR * sizeof(T) + sc * TR * sizeof(T) <= 200 * 1024;
-}
-
-// sc: vectors per CTA (8, 4, 2 or 1; 0 picks the largest within the default budget)
-template <typename T>
-cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, const int* bptr,
-                      const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
-                      const T* upsi, double sf, T* out, int sc, cudaStream_t st) {
-  constexpr int TR = BSE_K1D_TR;
-  if (n_vec <= 0) return cudaSuccess;
-  if (n3 % TR) return cudaErrorInvalidValue;
-  if (sc == 0) sc = k1d_vectors_per_cta<T>(n_occ);
-  if (!k1d_fits<T>(n_occ, sc)) return cudaErrorInvalidValue;
-  switch (sc) {
-    case 8: return launch_k1d<T, TR, 8>(n_vec, n_occ, n3, a, tau, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, out, st);
-    case 4: return launch_k1d<T, TR, 4>(n_vec, n_occ, n3, a, tau, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, out, st);
-    case 2: return launch_k1d<T, TR, 2>(n_vec, n_occ, n3, a, tau, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, out, st);
-    case 1: return launch_k1d<T, TR, 1>(n_vec, n_occ, n3, a, tau, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, out, st);
-    default: return cudaErrorInvalidValue;
+cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T* tau, long n_pairs, const int* bptr,
+                       const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
+                       const T* upsi, double sf, T* out, cudaStream_t st) {
+  static_assert(K1D_THREADS % TR == 0 && 32 % TR == 0 && K1D_THREADS / TR >= SC, "tile shape");
+  if constexpr (sizeof(T) == 8 && SC == 8) {
+    return cudaErrorInvalidValue;   // 64 double accumulators per lane do not fit the register budget
+  } else {
+    const size_t smem = ((size_t)n_occ * TR * SC + (size_t)TR * SC) * sizeof(T);
+    static std::once_flag once;
+    static cudaError_t once_st = cudaSuccess;
+    cudaError_t e0 = once_status(once, once_st, [&] {
+      return cudaFuncSetAttribute(k1d_tile_kernel<T, TR, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)K1D_SMEM_MAX);
+    });
+    if (e0 != cudaSuccess) return e0;
+    const long blocks = (n3 / TR) * ((n_vec + SC - 1) / SC);
+    k1d_tile_kernel<T, TR, SC><<<(unsigned)blocks, K1D_THREADS, smem, st>>>(
+        n_vec, n_occ, n3, a, tau, n_pairs, bptr, bw, bp, n_blocks, vloc, vh, upsi, (T)sf, out);
+    note_launch();
+    return cudaGetLastError();
   }
 }
 
-template cudaError_t k1d_tiled<float>(int, int, long, const float*, const float*, const int*, const int*, const int4*, int, const float*, const float*, const float*, double, float*, int, cudaStream_t);
-template cudaError_t k1d_tiled<double>(int, int, long, const double*, const double*, const int*, const int*, const int4*, int, const double*, const double*, const double*, double, double*, int, cudaStream_t);
+}  // namespace
+
+int k1d_num_variants() { return kNumVariants; }
+
+// whether variant v (1 .. k1d_num_variants()) fits the opt-in shared memory
+template <typename T>
+bool k1d_fits(int n_occ, int v) {
+  if (v < 1 || v > kNumVariants) return false;
+  if (sizeof(T) == 8 && kVariants[v].sc == 8) return false;
+  return variant_smem<T>(n_occ, v) <= K1D_SMEM_MAX;
+}
+
+// default variant without tuning: the first in the list whose a(r) stage leaves room for
+// two CTAs per SM, else the first that fits at all; 0 when none fits
+template <typename T>
+int k1d_default_variant(int n_occ) {
+  for (int v = 1; v <= kNumVariants; ++v)
+    if (k1d_fits<T>(n_occ, v) && variant_smem<T>(n_occ, v) <= K1D_SMEM_MAX / 2) return v;
+  for (int v = 1; v <= kNumVariants; ++v)
+    if (k1d_fits<T>(n_occ, v)) return v;
+  return 0;
+}
+
+template <typename T>
+cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, long n_pairs, const int* bptr,
+                      const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
+                      const T* upsi, double sf, T* out, int variant, cudaStream_t st) {
+  if (n_vec <= 0) return cudaSuccess;
+  if (variant == 0) variant = k1d_default_variant<T>(n_occ);
+  if (!k1d_fits<T>(n_occ, variant)) return cudaErrorInvalidValue;
+  if (n3 % TAU_TB || TAU_TB % kVariants[variant].tr) return cudaErrorInvalidValue;
+#define BSE_K1D_CASE(V, TR, SC)                                                                      \
+  case V:                                                                                            \
+    return launch_k1d<T, TR, SC>(n_vec, n_occ, n3, a, tau, n_pairs, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, \
+                                 out, st);
+  switch (variant) {
+    BSE_K1D_CASE(1, 16, 8)
+    BSE_K1D_CASE(2, 8, 8)
+    BSE_K1D_CASE(3, 16, 4)
+    BSE_K1D_CASE(4, 8, 4)
+    BSE_K1D_CASE(5, 16, 2)
+    BSE_K1D_CASE(6, 16, 1)
+    default: return cudaErrorInvalidValue;
+  }
+#undef BSE_K1D_CASE
+}
+
+template cudaError_t k1d_tiled<float>(int, int, long, const float*, const float*, long, const int*, const int*, const int4*, int, const float*, const float*, const float*, double, float*, int, cudaStream_t);
+template cudaError_t k1d_tiled<double>(int, int, long, const double*, const double*, long, const int*, const int*, const int4*, int, const double*, const double*, const double*, double, double*, int, cudaStream_t);
 template bool k1d_fits<float>(int, int);
 template bool k1d_fits<double>(int, int);
-template int k1d_vectors_per_cta<float>(int);
-template int k1d_vectors_per_cta<double>(int);
+template int k1d_default_variant<float>(int);
+template int k1d_default_variant<double>(int);
 
 }  // namespace bse

@@ -35,14 +35,15 @@ template <typename T>
 cudaError_t pair_product(int nb, const int* pv, const int* pw, const T* upsi, long n3, double scale,
                          cplx<T>* grids, cudaStream_t st);
 template <typename T>
-cudaError_t deinterleave_pairs(int nb, const cplx<T>* grids, long n3, T* tau, cudaStream_t st);
+cudaError_t deinterleave_pairs(int nb, const cplx<T>* grids, long n3, long p0, long n_pairs, T* tau,
+                               cudaStream_t st);
 cudaError_t square_fields(int n, const double* u, long n3, double* rho, cudaStream_t st);
 cudaError_t normalize_overlap(int n, double* gram, double* diag, cudaStream_t st);
 template <typename T>
 cudaError_t hartree_density(int n_vec, int n_occ, long n3, const T* a, const T* upsi, T* h,
                             cudaStream_t st);
 template <typename T>
-cudaError_t k1d_combine(int n_vec, int n_occ, long n3, const T* a, const T* tau, const int* nbr_ptr,
+cudaError_t k1d_combine(int n_vec, int n_occ, long n3, const T* a, const T* tau, long n_pairs, const int* nbr_ptr,
                         const int* nbr_w, const int* nbr_p, const T* vloc, const T* vh,
                         const T* upsi, double spin_factor, T* out, cudaStream_t st);
 // ---- tc_gemm.cu (tcgen05 BF16x3) ----
@@ -88,14 +89,16 @@ cudaError_t shift_scale(int ns, int nr, double* C, const double* lam, const doub
 cudaError_t row_dots(int ns, long dim, const double* A, const double* B, double* out, cudaStream_t st);
 
 // ---- k1d.cu ----
+// tile variants of the K1d kernel, numbered 1 .. k1d_num_variants(); 0 = default
+int k1d_num_variants();
 template <typename T>
-int k1d_vectors_per_cta(int n_occ);
+int k1d_default_variant(int n_occ);
 template <typename T>
-bool k1d_fits(int n_occ, int sc);
+bool k1d_fits(int n_occ, int variant);
 template <typename T>
-cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, const int* bptr,
+cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, long n_pairs, const int* bptr,
                       const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
-                      const T* upsi, double sf, T* out, int sc, cudaStream_t st);
+                      const T* upsi, double sf, T* out, int variant, cudaStream_t st);
 template <typename T>
 cudaError_t scale_columns(int rows, int cols, T* C, long ldc, const double* f, cudaStream_t st);
 template <typename TI, typename TO>

@@ -40,22 +40,25 @@ cudaError_t pair_product(int nb, const int* pv, const int* pw, const T* upsi, lo
   return cudaGetLastError();
 }
 
+// pairs p0 .. p0+nb-1 (two per complex grid) into the point-tiled tau array
 template <typename T>
-__global__ void deinterleave_kernel(int nb, const cplx<T>* __restrict__ grids, long n3,
-                                    T* __restrict__ tau) {
+__global__ void deinterleave_kernel(int nb, const cplx<T>* __restrict__ grids, long n3, long p0,
+                                    long n_pairs, T* __restrict__ tau) {
   const long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long c = blockIdx.y;
   if (r >= n3) return;
   const cplx<T> F = grids[c * n3 + r];
-  tau[(2 * c) * n3 + r] = F.x;
-  if (2 * c + 1 < nb) tau[(2 * c + 1) * n3 + r] = F.y;
+  tau[tau_off(p0 + 2 * c, r, n_pairs)] = F.x;
+  if (2 * c + 1 < nb) tau[tau_off(p0 + 2 * c + 1, r, n_pairs)] = F.y;
 }
 
 template <typename T>
-cudaError_t deinterleave_pairs(int nb, const cplx<T>* grids, long n3, T* tau, cudaStream_t st) {
+cudaError_t deinterleave_pairs(int nb, const cplx<T>* grids, long n3, long p0, long n_pairs, T* tau,
+                               cudaStream_t st) {
   if (nb <= 0) return cudaSuccess;
+  if (n3 % TAU_TB) return cudaErrorInvalidValue;
   dim3 grid(nblk(n3), (nb + 1) / 2);
-  deinterleave_kernel<T><<<grid, 256, 0, st>>>(nb, grids, n3, tau); note_launch();
+  deinterleave_kernel<T><<<grid, 256, 0, st>>>(nb, grids, n3, p0, n_pairs, tau); note_launch();
   return cudaGetLastError();
 }
 
@@ -125,7 +128,7 @@ cudaError_t hartree_density(int n_vec, int n_occ, long n3, const T* a, const T* 
 // ---------------------------------------------------------------------------------
 template <typename T, int SCH>
 __global__ void __launch_bounds__(256) k1d_combine_kernel(
-    int n_vec, int n_occ, long n3, const T* __restrict__ a, const T* __restrict__ tau,
+    int n_vec, int n_occ, long n3, const T* __restrict__ a, const T* __restrict__ tau, long n_pairs,
     const int* __restrict__ nbr_ptr, const int* __restrict__ nbr_w, const int* __restrict__ nbr_p,
     const T* __restrict__ vloc, const T* __restrict__ vh, const T* __restrict__ upsi, T sf,
     T* __restrict__ out) {
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(256) k1d_combine_kernel(
   const int e0 = nbr_ptr[v], e1 = nbr_ptr[v + 1];
   for (int e = e0; e < e1; ++e) {
     const int w = nbr_w[e];
-    const T t = tau[(long)nbr_p[e] * n3 + r];
+    const T t = tau[tau_off(nbr_p[e], r, n_pairs)];
 #pragma unroll
     for (int j = 0; j < SCH; ++j) {
       const int s = s0 + j;
@@ -158,13 +161,13 @@ __global__ void __launch_bounds__(256) k1d_combine_kernel(
 }
 
 template <typename T>
-cudaError_t k1d_combine(int n_vec, int n_occ, long n3, const T* a, const T* tau, const int* nbr_ptr,
+cudaError_t k1d_combine(int n_vec, int n_occ, long n3, const T* a, const T* tau, long n_pairs, const int* nbr_ptr,
                         const int* nbr_w, const int* nbr_p, const T* vloc, const T* vh,
                         const T* upsi, double spin_factor, T* out, cudaStream_t st) {
   constexpr int SCH = 8;
   if (!n_vec) return cudaSuccess;
   dim3 grid(nblk(n3), n_occ, (n_vec + SCH - 1) / SCH);
-  k1d_combine_kernel<T, SCH><<<grid, 256, 0, st>>>(n_vec, n_occ, n3, a, tau, nbr_ptr, nbr_w, nbr_p,
+  k1d_combine_kernel<T, SCH><<<grid, 256, 0, st>>>(n_vec, n_occ, n3, a, tau, n_pairs, nbr_ptr, nbr_w, nbr_p,
                                                    vloc, vh, upsi, (T)spin_factor, out); note_launch();
   return cudaGetLastError();
 }
@@ -461,9 +464,9 @@ bool finite_check_host(const double* x, long n) {
 #define INST_T(T)                                                                                  \
   template cudaError_t pair_product<T>(int, const int*, const int*, const T*, long, double,        \
                                        cplx<T>*, cudaStream_t);                                    \
-  template cudaError_t deinterleave_pairs<T>(int, const cplx<T>*, long, T*, cudaStream_t);         \
+  template cudaError_t deinterleave_pairs<T>(int, const cplx<T>*, long, long, long, T*, cudaStream_t);       \
   template cudaError_t hartree_density<T>(int, int, long, const T*, const T*, T*, cudaStream_t);   \
-  template cudaError_t k1d_combine<T>(int, int, long, const T*, const T*, const int*, const int*,   \
+  template cudaError_t k1d_combine<T>(int, int, long, const T*, const T*, long, const int*, const int*,   \
                                       const int*, const T*, const T*, const T*, double, T*,        \
                                       cudaStream_t);                                               \
   template cudaError_t scale_columns<T>(int, int, T*, long, const double*, cudaStream_t);          \
