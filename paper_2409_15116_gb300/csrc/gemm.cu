@@ -158,12 +158,259 @@ static cudaError_t dispatch_t(bool at, bool bt, int M, int N, int K, double alph
   return launch<T, TC, true, true, TM, TN, DF>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk, st);
 }
 
+// ---------------------------------------------------------------------------------
+// Tall-skinny products of the Davidson algebra in single precision.
+//
+// ts_tn:  C (M x N, double) = alpha A B^T + beta C with A M x K, B N x K, N <= 32 and K
+//         in the millions (Gram, Rayleigh-Ritz and CGS coefficient matrices). A CTA takes
+//         a 2048-long stretch of K and a 64-row tile of A, streamed through a four-stage
+//         cp.async ring in 32-wide chunks; each warp computes the whole 64 x 32 tile on
+//         its own 4-wide slice of every chunk (lane: 8 x 8 outputs as packed FP32 pairs),
+//         so every accumulator sums 256 products in FP32; the eight warp partials are
+//         added in double and accumulated into C with double-precision atomics.
+// ts_nn:  C (M x N) = alpha op(A) B + beta C with op(A) M x K small (K <= 256) and N in the
+//         millions (CGS update, Cholesky-QR, Ritz vectors, restart). op(A) sits in shared
+//         memory; a thread owns four adjacent columns and a band of up to 16 rows,
+//         streaming B straight from global memory in 16-byte loads.
+// ---------------------------------------------------------------------------------
+namespace {
+
+constexpr int TS_KS = 2048;    // K per CTA (ts_tn)
+constexpr int TS_KC = 32;      // K per staged chunk
+constexpr int TS_BM = 64;      // rows of A per CTA
+constexpr int TS_STAGES = 4;
+
+// staged chunk row: 32 floats in eight 16-byte groups, group g stored at g ^ (row/8 % 8),
+// so that lanes reading the same group of eight different rows hit distinct banks
+__device__ __forceinline__ int ts_off(int row, int g) { return row * TS_KC + ((g ^ ((row >> 3) & 7)) << 2); }
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;   // 0: fill the 16 bytes with zeros, read nothing
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+}
+
+__global__ void __launch_bounds__(256, 2) ts_gemm_tn_kernel(int M, int N, long K, double alpha,
+                                                           const float* __restrict__ A, long lda,
+                                                           const float* __restrict__ B, long ldb,
+                                                           double* __restrict__ C, long ldc) {
+  extern __shared__ __align__(16) float ts_smem[];
+  constexpr int STAGE = (TS_BM + 32) * TS_KC;       // floats per stage: A rows then B rows
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long i0 = (long)blockIdx.y * TS_BM;
+  const long kbeg = (long)blockIdx.x * TS_KS;
+  const long kend = min(K, kbeg + TS_KS);
+  const int nch = (int)((kend - kbeg + TS_KC - 1) / TS_KC);
+  // copies of one chunk: 96 rows x 8 groups = 768 16-byte pieces, three per thread
+  auto issue = [&](int ch) {
+    float* st = ts_smem + (ch % TS_STAGES) * STAGE;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int e = tid + 256 * q;
+      const int row = e >> 3, g = e & 7;
+      const long k = kbeg + (long)ch * TS_KC + 4 * g;
+      const float* src;
+      bool ok;
+      if (row < TS_BM) {
+        const long i = i0 + row;
+        ok = (i < M) && (k < kend);
+        src = ok ? A + i * lda + k : A;
+      } else {
+        const int j = row - TS_BM;
+        ok = (j < N) && (k < kend);
+        src = ok ? B + (long)j * ldb + k : B;
+      }
+      cp_async16(st + ts_off(row, g), src, ok);
+    }
+  };
+#pragma unroll
+  for (int s0 = 0; s0 < TS_STAGES - 1; ++s0) {
+    if (s0 < nch) issue(s0);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  const int ib = lane >> 2, jb = lane & 3;
+  float2 acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (int ch = 0; ch < nch; ++ch) {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(TS_STAGES - 2) : "memory");
+    __syncthreads();
+    if (ch + TS_STAGES - 1 < nch) issue(ch + TS_STAGES - 1);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    const float* as = ts_smem + (ch % TS_STAGES) * STAGE;
+    const float* bs = as + TS_BM * TS_KC;
+    // this warp's four k values: group `warp` of every row
+    float2 bp[4][4];    // [k][j pair]
+#pragma unroll
+    for (int jp = 0; jp < 4; ++jp) {
+      const float4 u = *reinterpret_cast<const float4*>(bs + ts_off(8 * jb + 2 * jp, warp));
+      const float4 v = *reinterpret_cast<const float4*>(bs + ts_off(8 * jb + 2 * jp + 1, warp));
+      bp[0][jp] = make_float2(u.x, v.x);
+      bp[1][jp] = make_float2(u.y, v.y);
+      bp[2][jp] = make_float2(u.z, v.z);
+      bp[3][jp] = make_float2(u.w, v.w);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float4 a = *reinterpret_cast<const float4*>(as + ts_off(8 * ib + i, warp));
+      const float ak[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const float2 ai = make_float2(ak[kk], ak[kk]);
+#pragma unroll
+        for (int jp = 0; jp < 4; ++jp) acc[i][jp] = __ffma2_rn(ai, bp[kk][jp], acc[i][jp]);
+      }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  // eight warp partials -> double sums -> atomics
+  float* red = ts_smem;                              // [8][64][32]
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int jp = 0; jp < 4; ++jp)
+      *reinterpret_cast<float2*>(red + ((size_t)warp * 64 + 8 * ib + i) * 32 + 8 * jb + 2 * jp) = acc[i][jp];
+  __syncthreads();
+  for (int o = tid; o < 64 * 32; o += 256) {
+    const int i = o >> 5, j = o & 31;
+    if (i0 + i >= M || j >= N) continue;
+    double sum = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) sum += (double)red[w * 64 * 32 + o];
+    atomicAdd(C + (i0 + i) * ldc + j, alpha * sum);
+  }
+}
+
+template <int MT, bool AT>
+__global__ void __launch_bounds__(256) ts_gemm_nn_kernel(int M, long N, int K, double alpha,
+                                                        const float* __restrict__ A, long lda,
+                                                        const float* __restrict__ B, long ldb,
+                                                        double beta, float* __restrict__ C, long ldc) {
+  extern __shared__ __align__(16) float ts_smem[];
+  float* S = ts_smem;                                // [K][MT]: op(A)[i0 + i][k]
+  const int i0 = blockIdx.x * MT;                    // row band (fastest: bands share B in L2)
+  for (int e = threadIdx.x; e < K * MT; e += 256) {
+    const int k = e / MT, i = e - k * MT;
+    const int gi = i0 + i;
+    S[e] = (gi < M) ? (AT ? A[(long)k * lda + gi] : A[(long)gi * lda + k]) : 0.f;
+  }
+  __syncthreads();
+  const long d = 4 * ((long)blockIdx.y * 256 + threadIdx.x);
+  if (d >= N) return;
+  float2 acc[MT][2];
+#pragma unroll
+  for (int i = 0; i < MT; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
+  const float* bp = B + d;
+  int k = 0;
+  for (; k + 4 <= K; k += 4) {
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const float4*>(bp + (long)(k + u) * ldb);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float* sk = S + (k + u) * MT;
+      const float2 v0 = make_float2(v[u].x, v[u].y), v1 = make_float2(v[u].z, v[u].w);
+#pragma unroll
+      for (int i = 0; i < MT; i += 4) {
+        const float4 s4 = *reinterpret_cast<const float4*>(sk + i);
+        const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 sq = make_float2(sv[q], sv[q]);
+          acc[i + q][0] = __ffma2_rn(sq, v0, acc[i + q][0]);
+          acc[i + q][1] = __ffma2_rn(sq, v1, acc[i + q][1]);
+        }
+      }
+    }
+  }
+  for (; k < K; ++k) {
+    const float4 v = *reinterpret_cast<const float4*>(bp + (long)k * ldb);
+    const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
+    const float* sk = S + k * MT;
+#pragma unroll
+    for (int i = 0; i < MT; ++i) {
+      const float2 sq = make_float2(sk[i], sk[i]);
+      acc[i][0] = __ffma2_rn(sq, v0, acc[i][0]);
+      acc[i][1] = __ffma2_rn(sq, v1, acc[i][1]);
+    }
+  }
+  const float al = (float)alpha, be = (float)beta;
+#pragma unroll
+  for (int i = 0; i < MT; ++i) {
+    if (i0 + i >= M) break;
+    float4* cp = reinterpret_cast<float4*>(C + (long)(i0 + i) * ldc + d);
+    float4 r = make_float4(al * acc[i][0].x, al * acc[i][0].y, al * acc[i][1].x, al * acc[i][1].y);
+    if (be != 0.f) {
+      const float4 c0 = *cp;
+      r.x += be * c0.x; r.y += be * c0.y; r.z += be * c0.z; r.w += be * c0.w;
+    }
+    *cp = r;
+  }
+}
+
+bool aligned(const void* p, size_t b) { return ((uintptr_t)p % b) == 0; }
+
+// C = alpha A B^T + beta C, A M x K, B N x K (both row-major), N <= 32
+cudaError_t ts_gemm_tn(int M, int N, long K, double alpha, const float* A, long lda, const float* B,
+                       long ldb, double beta, double* C, long ldc, cudaStream_t st) {
+  const long tot = (long)M * N;
+  scale_matrix_kernel<double><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, C, ldc, beta); note_launch();
+  if (K == 0) return cudaGetLastError();
+  // the reduction area (8 x 64 x 32 floats) covers the four staging buffers
+  constexpr size_t smem = 8 * 64 * 32 * sizeof(float);
+  static_assert(smem >= (size_t)TS_STAGES * (TS_BM + 32) * TS_KC * sizeof(float), "smem");
+  static std::once_flag once;
+  static cudaError_t once_st = cudaSuccess;
+  cudaError_t e0 = once_status(once, once_st, [&] {
+    return cudaFuncSetAttribute(ts_gemm_tn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e0 != cudaSuccess) return e0;
+  dim3 grid((unsigned)((K + TS_KS - 1) / TS_KS), (unsigned)((M + TS_BM - 1) / TS_BM));
+  ts_gemm_tn_kernel<<<grid, 256, smem, st>>>(M, N, K, alpha, A, lda, B, ldb, C, ldc); note_launch();
+  return cudaGetLastError();
+}
+
+template <int MT>
+cudaError_t ts_nn_launch(bool at, int M, long N, int K, double alpha, const float* A, long lda,
+                         const float* B, long ldb, double beta, float* C, long ldc, cudaStream_t st) {
+  const size_t smem = (size_t)K * MT * sizeof(float);
+  dim3 grid((unsigned)((M + MT - 1) / MT), (unsigned)((N / 4 + 255) / 256));
+  if (at) ts_gemm_nn_kernel<MT, true><<<grid, 256, smem, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else ts_gemm_nn_kernel<MT, false><<<grid, 256, smem, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// C = alpha op(A) B + beta C, op(A) M x K (A stored K x M when at), B K x N row-major
+cudaError_t ts_gemm_nn(bool at, int M, long N, int K, double alpha, const float* A, long lda,
+                       const float* B, long ldb, double beta, float* C, long ldc, cudaStream_t st) {
+  if (M <= 4) return ts_nn_launch<4>(at, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+  if (M <= 8) return ts_nn_launch<8>(at, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+  return ts_nn_launch<16>(at, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+}
+
+}  // namespace
+
 // Tile shape follows the operands: a side of at most 16 gets a 16-wide tile, so the
 // tall-skinny products of the Davidson algebra (16-32 rows against millions of
 // columns) do not pad a 64-wide tile.
 template <typename T, typename TC>
 cudaError_t gemm(bool at, bool bt, int M, int N, int K, double alpha, const T* A, long lda,
                  const T* B, long ldb, double beta, TC* C, long ldc, int splitk, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if constexpr (sizeof(T) == 4 && sizeof(TC) == 8) {
+    if (!at && bt && N <= 32 && K >= 4096 && K % 4 == 0 && lda % 4 == 0 && ldb % 4 == 0 &&
+        aligned(A, 16) && aligned(B, 16))
+      return ts_gemm_tn(M, N, K, alpha, (const float*)A, lda, (const float*)B, ldb, beta, (double*)C, ldc, st);
+  }
+  if constexpr (sizeof(T) == 4 && sizeof(TC) == 4) {
+    if (!bt && M <= 64 && K <= 256 && N >= 1024 && N / 1024 < 65535 && N % 4 == 0 && ldb % 4 == 0 && ldc % 4 == 0 &&
+        aligned(B, 16) && aligned(C, 16))
+      return ts_gemm_nn(at, M, N, K, alpha, (const float*)A, lda, (const float*)B, ldb, beta, (float*)C, ldc, st);
+  }
   const bool sm = M <= 16, sn = N <= 16;
   if (sm && !sn) return dispatch_t<T, TC, 1, 4>(at, bt, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk, st);
   if (sn && !sm) return dispatch_t<T, TC, 4, 1>(at, bt, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk, st);
