@@ -95,6 +95,7 @@ struct bse_ctx {
   bool tau_ready = false;
   // device, common
   int *gpos = nullptr, *gneg = nullptr;
+  SphereMap sph;             // column-ordered sphere for the pruned transforms
   double *g2p = nullptr, *eps = nullptr, *f = nullptr;
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
@@ -386,13 +387,11 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
     cplx<T>* gh = (cplx<T>*)c->ws_h;
     const double sz = sizeof(T), gb = (double)ngr * n3 * sizeof(cplx<T>);
     // a_sv(G) -> a_sv(r)
+    // a_sv(G) -> a_sv(r): pruned transform, compact stages in the (not yet used) R(r) grids
     {
-      Scope sc(c, "sphere_unpack", (double)nf * c->n_pw * sz + gb, 0.0);
-      CK((sphere_unpack<T, T>(ain, nf, c->n_pw, c->n_half, c->gpos, c->gneg, ga, n3, true, false, c->st)));
-    }
-    {
-      Scope sc(c, "fft_inverse_a", 2.0 * gb, fft_flops(n3, ngr));
-      CK(fft3d<T>(ga, ngr, N, +1, tw_of<T>(c), c->st));
+      const double gsc = gb * (double)sphere_scratch_per_grid(N, c->sph) / (double)n3;
+      Scope sc(c, "fft_inverse_a", (double)nf * c->n_pw * sz + gb + 2.0 * gsc, fft_flops(n3, ngr));
+      CK(sphere_to_grid<T>(ain, nf, c->n_pw, c->n_half, N, c->sph, tw_of<T>(c), gr, ga, c->st));
     }
     // Hartree potential of the pair density sum_w psi_w a_sw (Eq. k1e)
     const long nh = (nv + 1) / 2;
@@ -425,14 +424,13 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
       }
     }
     // back to the sphere, plus (1/2|G|^2 + Delta - eps_v) a (Eq. d)
+    // back to the sphere, plus (1/2|G|^2 + Delta - eps_v) a (Eq. d); compact stages in
+    // the a(r) grids, which K1d no longer needs
     {
-      Scope sc(c, "fft_forward_r", 2.0 * gb, fft_flops(n3, ngr));
-      CK(fft3d<T>(gr, ngr, N, -1, tw_of<T>(c), c->st));
-    }
-    {
-      Scope sc(c, "sphere_pack_d", gb + 2.0 * nf * c->n_pw * sz, 4.0 * nf * c->n_pw);
-      CK((sphere_pack<T, T>(gr, nf, c->n_pw, c->n_half, c->gpos, c->gneg, n3, 1.0 / (double)n3, aout,
-                            ain, c->g2p, c->eps, c->scissor, c->n_occ, c->st)));
+      const double gsc = gb * (double)sphere_scratch_per_grid(N, c->sph) / (double)n3;
+      Scope sc(c, "fft_forward_r", gb + 2.0 * gsc + 3.0 * nf * c->n_pw * sz, fft_flops(n3, ngr));
+      CK(grid_to_sphere<T>(gr, nf, c->n_pw, c->n_half, N, c->sph, tw_of<T>(c), ga, 1.0 / (double)n3, aout,
+                           ain, c->g2p, c->eps, c->scissor, c->n_occ, c->st));
     }
     {
       Scope sc(c, "projector_pc", (3.0 * nf * c->n_pw + (double)c->n_occ * c->n_pw) * sz,
@@ -988,6 +986,23 @@ int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) 
   } while (0)
   UPLOAD(c->gpos, gpos.data(), c->n_half);
   UPLOAD(c->gneg, gneg.data(), c->n_half);
+  {
+    SphereMapHost h;
+    build_sphere_map(c->N, c->n_half, s->miller, h);
+    if (sphere_scratch_per_grid(c->N, SphereMap{h.NS, h.NC, h.NX}) > (size_t)c->n3)
+      return bail(fail(c, BSE_ERR_INVALID_ARG, "sphere too large for the pruned transforms"));
+    int *fp, *fn, *zs, *jc, *cs, *cy, *cx, *xs, *xc;
+    UPLOAD(fp, h.fpos.data(), h.fpos.size());
+    UPLOAD(fn, h.fneg.data(), h.fneg.size());
+    UPLOAD(zs, h.zs.data(), h.zs.size());
+    UPLOAD(jc, h.jcol.data(), h.jcol.size());
+    UPLOAD(cs, h.cstart.data(), h.cstart.size());
+    UPLOAD(cy, h.cy.data(), h.cy.size());
+    UPLOAD(cx, h.cxi.data(), h.cxi.size());
+    UPLOAD(xs, h.xs.data(), h.xs.size());
+    UPLOAD(xc, h.xcol.data(), h.xcol.size());
+    c->sph = SphereMap{h.NS, h.NC, h.NX, fp, fn, zs, jc, cs, cy, cx, xs, xc};
+  }
   UPLOAD(c->g2p, c->g2p_h.data(), c->n_pw);
   UPLOAD(c->eps, s->eps, c->n_occ);
   UPLOAD(c->f, fh.data(), fh.size());
@@ -1495,10 +1510,10 @@ int apply_static_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out, unsigned 
   T* cb = reinterpret_cast<T*>(ws + 2 * b_a + b_h);
   const int N = c->N;
   const double sf = (c->spin == 0) ? 2.0 : 0.0;
-  // the array keeps the previous call's contents: everything read before it is
-  // written is cleared here (the a(r) and Hartree grids, the odd tail of R(r))
-  CK((sphere_unpack<T, T>(a_in, nf, c->n_pw, c->n_half, c->gpos, c->gneg, ga, n3, true, false, c->st)));
-  CK(fft3d<T>(ga, ngr, N, +1, tw_of<T>(c), c->st));
+  // the array keeps the previous call's contents: everything read is written first (the
+  // transforms write every compact stage and grid point they read back) or cleared here
+  // (the Hartree grids, the odd tail of R(r))
+  CK(sphere_to_grid<T>(a_in, nf, c->n_pw, c->n_half, N, c->sph, tw_of<T>(c), gr, ga, c->st));
   CK(cudaMemsetAsync(gh, 0, (size_t)nh * n3 * sizeof(cplx<T>), c->st));
   if (sf != 0.0) {
     CK(hartree_density<T>((int)n_vec, c->n_occ, n3, (const T*)ga, upsi_of<T>(c), (T*)gh, c->st));
@@ -1515,9 +1530,8 @@ int apply_static_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out, unsigned 
     CK(k1d_combine<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, c->n_pairs, c->nbr_ptr, c->nbr_w,
                       c->nbr_p, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
   }
-  CK(fft3d<T>(gr, ngr, N, -1, tw_of<T>(c), c->st));
-  CK((sphere_pack<T, T>(gr, nf, c->n_pw, c->n_half, c->gpos, c->gneg, n3, 1.0 / (double)n3, a_out,
-                        a_in, c->g2p, c->eps, c->scissor, c->n_occ, c->st)));
+  CK(grid_to_sphere<T>(gr, nf, c->n_pw, c->n_half, N, c->sph, tw_of<T>(c), ga, 1.0 / (double)n3, a_out,
+                       a_in, c->g2p, c->eps, c->scissor, c->n_occ, c->st));
   // P_c with the SIMT GEMM (the tensor-core path would allocate split buffers)
   const T* psi = psi_of<T>(c);
   CK((gemm<T, T>(false, true, (int)nf, c->n_occ, c->n_pw, 1.0, a_out, c->n_pw, psi, c->n_pw, 0.0, cb,

@@ -14,6 +14,7 @@
 // part = odd field); they separate again through Hermitian symmetry at the sphere.
 #include "common.cuh"
 #include "kernels.h"
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -100,6 +101,29 @@ __device__ __forceinline__ void stage(const C* src, C* dst, const C* tw, int Ns,
   }
 }
 
+// all stages of the TX lines held in buf0 (buf1 is scratch); returns the buffer holding
+// the result. Ends with a barrier.
+template <typename C, int N>
+__device__ __forceinline__ const C* line_fft(C* buf0, C* buf1, const C* tw, int sign) {
+  constexpr int TX = Plan<N>::TX;
+  C* src = buf0; C* dst = buf1;
+  int Ns = 1;
+  stage<C, N, Plan<N>::r0, TX>(src, dst, tw, Ns, sign);
+  __syncthreads();
+  { C* t = src; src = dst; dst = t; } Ns *= Plan<N>::r0;
+  if constexpr (Plan<N>::n > 1) {
+    stage<C, N, Plan<N>::r1, TX>(src, dst, tw, Ns, sign);
+    __syncthreads();
+    { C* t = src; src = dst; dst = t; } Ns *= Plan<N>::r1;
+  }
+  if constexpr (Plan<N>::n > 2) {
+    stage<C, N, Plan<N>::r2, TX>(src, dst, tw, Ns, sign);
+    __syncthreads();
+    { C* t = src; src = dst; dst = t; }
+  }
+  return src;
+}
+
 template <typename T, int N>
 __global__ void __launch_bounds__(256) fft_axis_kernel(cplx<T>* __restrict__ data, int axis,
                                                       int sign, const cplx<T>* __restrict__ table) {
@@ -134,21 +158,7 @@ __global__ void __launch_bounds__(256) fft_axis_kernel(cplx<T>* __restrict__ dat
     buf0[sidx<N>(i, k)] = data[base + i * si + k * sk];
   }
   __syncthreads();
-  C* src = buf0; C* dst = buf1;
-  int Ns = 1;
-  stage<C, N, Plan<N>::r0, TX>(src, dst, tw, Ns, sign);
-  __syncthreads();
-  { C* t = src; src = dst; dst = t; } Ns *= Plan<N>::r0;
-  if constexpr (Plan<N>::n > 1) {
-    stage<C, N, Plan<N>::r1, TX>(src, dst, tw, Ns, sign);
-    __syncthreads();
-    { C* t = src; src = dst; dst = t; } Ns *= Plan<N>::r1;
-  }
-  if constexpr (Plan<N>::n > 2) {
-    stage<C, N, Plan<N>::r2, TX>(src, dst, tw, Ns, sign);
-    __syncthreads();
-    { C* t = src; src = dst; dst = t; }
-  }
+  const C* src = line_fft<C, N>(buf0, buf1, tw, sign);
   for (int e = threadIdx.x; e < TX * N; e += blockDim.x) {
     int i, k;
     if (axis == 0) { i = e / N; k = e - i * N; } else { k = e / TX; i = e - k * TX; }
@@ -190,6 +200,287 @@ cudaError_t fft3d(cplx<T>* data, long n_batch, int N, int sign, const cplx<T>* t
 }
 template cudaError_t fft3d<float>(float2*, long, int, int, const float2*, cudaStream_t);
 template cudaError_t fft3d<double>(double2*, long, int, int, const double2*, cudaStream_t);
+
+// ---------------------------------------------------------------------------------
+// Pruned transforms between the plane-wave sphere and the grid.
+//
+// A field on the sphere occupies few grid lines: its (x, y) columns form a disc and its
+// x values a band of at most N/2. The sphere -> grid transform therefore runs z lines
+// only for the sphere's columns, y lines only for x in the band, and x lines for the
+// whole grid; the grid -> sphere transform runs the same lines in the opposite order,
+// keeping only what the next pass reads. Per complex grid g the compact stages are
+//   S [NS]          the full sphere (+G and -G), ordered by column, then z
+//   I1[N][NC]       z-transformed columns             (z, column)
+//   I2[N][N][NX]    y-transformed band                (z, y, x slot)
+// and each transformed line is exactly the zero-padded full-grid line's transform.
+// ---------------------------------------------------------------------------------
+
+template <typename C, int N>
+__device__ __forceinline__ void load_twiddles(C* tw, const C* table, int sign) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    C t = table[i];
+    if (sign > 0) t.y = -t.y;
+    tw[i] = t;
+  }
+}
+
+template <typename C, int N>
+__device__ __forceinline__ void zero_lines(C* buf) {
+  for (int e = threadIdx.x; e < Plan<N>::TX * Pad<N>::LS; e += blockDim.x) buf[e] = cmk<C>(0, 0);
+}
+
+// z lines of the sphere's columns. inverse: S -> I1; forward: I1 -> S
+template <typename T, int N, bool INV>
+__global__ void __launch_bounds__(256) sph_z_kernel(cplx<T>* __restrict__ S, cplx<T>* __restrict__ I1,
+                                                   SphereMap m, int sign, const cplx<T>* __restrict__ table) {
+  using C = cplx<T>;
+  constexpr int TL = Plan<N>::TX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + TL * Pad<N>::LS;
+  C* tw = buf1 + TL * Pad<N>::LS;
+  load_twiddles<C, N>(tw, table, sign);
+  const int nt = (m.NC + TL - 1) / TL;
+  const long g = blockIdx.x / nt;
+  const int c0 = (int)(blockIdx.x % nt) * TL;
+  const int nl = min(TL, m.NC - c0);
+  const int j0 = m.cstart[c0], j1 = m.cstart[c0 + nl];
+  C* Sg = S + g * m.NS;
+  C* I1g = I1 + g * (long)N * m.NC;
+  if (INV) {
+    zero_lines<C, N>(buf0);
+    __syncthreads();
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) buf0[sidx<N>(m.jcol[j] - c0, m.zs[j])] = Sg[j];
+  } else {
+    for (int e = threadIdx.x; e < TL * N; e += blockDim.x) {
+      const int l = e % TL, z = e / TL;
+      buf0[sidx<N>(l, z)] = (l < nl) ? I1g[(long)z * m.NC + c0 + l] : cmk<C>(0, 0);
+    }
+  }
+  __syncthreads();
+  const C* src = line_fft<C, N>(buf0, buf1, tw, sign);
+  if (INV) {
+    for (int e = threadIdx.x; e < TL * N; e += blockDim.x) {
+      const int l = e % TL, z = e / TL;
+      if (l < nl) I1g[(long)z * m.NC + c0 + l] = src[sidx<N>(l, z)];
+    }
+  } else {
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) Sg[j] = src[sidx<N>(m.jcol[j] - c0, m.zs[j])];
+  }
+}
+
+// y lines of the band. inverse: I1 -> I2; forward: I2 -> I1
+template <typename T, int N, bool INV>
+__global__ void __launch_bounds__(256) sph_y_kernel(cplx<T>* __restrict__ I1, cplx<T>* __restrict__ I2,
+                                                   SphereMap m, int sign, const cplx<T>* __restrict__ table) {
+  using C = cplx<T>;
+  constexpr int TL = Plan<N>::TX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + TL * Pad<N>::LS;
+  C* tw = buf1 + TL * Pad<N>::LS;
+  load_twiddles<C, N>(tw, table, sign);
+  const int nt = (m.NX + TL - 1) / TL;
+  const long gz = blockIdx.x / nt;                   // g * N + z
+  const int x0 = (int)(blockIdx.x % nt) * TL;
+  const int nl = min(TL, m.NX - x0);
+  const int ca = m.xcol[x0], cb = m.xcol[x0 + nl];
+  C* I1r = I1 + gz * m.NC;                           // I1[g][z][.]
+  C* I2r = I2 + gz * (long)N * m.NX;                 // I2[g][z][.][.]
+  if (INV) {
+    zero_lines<C, N>(buf0);
+    __syncthreads();
+    for (int c = ca + threadIdx.x; c < cb; c += blockDim.x) buf0[sidx<N>(m.cxi[c] - x0, m.cy[c])] = I1r[c];
+  } else {
+    for (int e = threadIdx.x; e < TL * N; e += blockDim.x) {
+      const int l = e % TL, y = e / TL;
+      buf0[sidx<N>(l, y)] = (l < nl) ? I2r[(long)y * m.NX + x0 + l] : cmk<C>(0, 0);
+    }
+  }
+  __syncthreads();
+  const C* src = line_fft<C, N>(buf0, buf1, tw, sign);
+  if (INV) {
+    for (int e = threadIdx.x; e < TL * N; e += blockDim.x) {
+      const int l = e % TL, y = e / TL;
+      if (l < nl) I2r[(long)y * m.NX + x0 + l] = src[sidx<N>(l, y)];
+    }
+  } else {
+    for (int c = ca + threadIdx.x; c < cb; c += blockDim.x) I1r[c] = src[sidx<N>(m.cxi[c] - x0, m.cy[c])];
+  }
+}
+
+// x lines of the whole grid. inverse: I2 -> grid; forward: grid -> I2
+template <typename T, int N, bool INV>
+__global__ void __launch_bounds__(256) sph_x_kernel(cplx<T>* __restrict__ I2, cplx<T>* __restrict__ grid,
+                                                   SphereMap m, int sign, const cplx<T>* __restrict__ table) {
+  using C = cplx<T>;
+  constexpr int TL = Plan<N>::TX;
+  static_assert(N % TL == 0, "line tile");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + TL * Pad<N>::LS;
+  C* tw = buf1 + TL * Pad<N>::LS;
+  load_twiddles<C, N>(tw, table, sign);
+  constexpr int nt = N / TL;
+  const long gz = blockIdx.x / nt;
+  const int y0 = (int)(blockIdx.x % nt) * TL;
+  C* I2r = I2 + (gz * N + y0) * m.NX;                // I2[g][z][y0 + l][xi]
+  C* Gr = grid + (gz * N + y0) * N;                  // grid[g][z][y0 + l][x]
+  if (INV) {
+    zero_lines<C, N>(buf0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < TL * m.NX; e += blockDim.x) {
+      const int l = e / m.NX, xi = e - l * m.NX;
+      buf0[sidx<N>(l, m.xs[xi])] = I2r[e];
+    }
+  } else {
+    for (int e = threadIdx.x; e < TL * N; e += blockDim.x) {
+      const int l = e / N, x = e - l * N;
+      buf0[sidx<N>(l, x)] = Gr[e];
+    }
+  }
+  __syncthreads();
+  const C* src = line_fft<C, N>(buf0, buf1, tw, sign);
+  if (INV) {
+    for (int e = threadIdx.x; e < TL * N; e += blockDim.x) {
+      const int l = e / N, x = e - l * N;
+      Gr[e] = src[sidx<N>(l, x)];
+    }
+  } else {
+    for (int e = threadIdx.x; e < TL * m.NX; e += blockDim.x) {
+      const int l = e / m.NX, xi = e - l * m.NX;
+      I2r[e] = src[sidx<N>(l, m.xs[xi])];
+    }
+  }
+}
+
+template <typename T, int N>
+static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>* I2, cplx<T>* grid,
+                                 long n_grids, const SphereMap& m, const cplx<T>* table, cudaStream_t st) {
+  constexpr int TL = Plan<N>::TX;
+  const size_t smem = (size_t)(2 * TL * Pad<N>::LS + N) * sizeof(cplx<T>);
+  static std::once_flag once;
+  static cudaError_t once_st = cudaSuccess;
+  cudaError_t e0 = once_status(once, once_st, [&] {
+    cudaError_t e = cudaSuccess;
+    const void* ks[6] = {(const void*)sph_z_kernel<T, N, true>, (const void*)sph_z_kernel<T, N, false>,
+                         (const void*)sph_y_kernel<T, N, true>, (const void*)sph_y_kernel<T, N, false>,
+                         (const void*)sph_x_kernel<T, N, true>, (const void*)sph_x_kernel<T, N, false>};
+    for (const void* k : ks)
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+  });
+  if (e0 != cudaSuccess) return e0;
+  if (n_grids <= 0) return cudaSuccess;
+  const long bz = n_grids * ((m.NC + TL - 1) / TL);
+  const long by = n_grids * N * ((m.NX + TL - 1) / TL);
+  const long bx = n_grids * N * (N / TL);
+  if (inverse) {
+    sph_z_kernel<T, N, true><<<(unsigned)bz, 256, smem, st>>>(S, I1, m, +1, table); note_launch();
+    sph_y_kernel<T, N, true><<<(unsigned)by, 256, smem, st>>>(I1, I2, m, +1, table); note_launch();
+    sph_x_kernel<T, N, true><<<(unsigned)bx, 256, smem, st>>>(I2, grid, m, +1, table); note_launch();
+  } else {
+    sph_x_kernel<T, N, false><<<(unsigned)bx, 256, smem, st>>>(I2, grid, m, -1, table); note_launch();
+    sph_y_kernel<T, N, false><<<(unsigned)by, 256, smem, st>>>(I1, I2, m, -1, table); note_launch();
+    sph_z_kernel<T, N, false><<<(unsigned)bz, 256, smem, st>>>(S, I1, m, -1, table); note_launch();
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>* I2, cplx<T>* grid, long n_grids,
+                          int N, const SphereMap& m, const cplx<T>* table, cudaStream_t st) {
+  switch (N) {
+    case 16: return launch_pruned<T, 16>(inverse, S, I1, I2, grid, n_grids, m, table, st);
+    case 32: return launch_pruned<T, 32>(inverse, S, I1, I2, grid, n_grids, m, table, st);
+    case 48: return launch_pruned<T, 48>(inverse, S, I1, I2, grid, n_grids, m, table, st);
+    case 64: return launch_pruned<T, 64>(inverse, S, I1, I2, grid, n_grids, m, table, st);
+    case 72: return launch_pruned<T, 72>(inverse, S, I1, I2, grid, n_grids, m, table, st);
+    case 96: return launch_pruned<T, 96>(inverse, S, I1, I2, grid, n_grids, m, table, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t sphere_scratch_per_grid(int N, const SphereMap& m) {
+  return (size_t)m.NS + (size_t)N * m.NC + (size_t)N * N * m.NX;
+}
+
+// packed fields (two per complex grid) -> real-space grids, unnormalised sign +1 transform.
+// scratch: n_grids * sphere_scratch_per_grid complex values, disjoint from grids.
+template <typename T>
+cudaError_t sphere_to_grid(const T* P, long n_fields, int n_pw, int n_half, int N, const SphereMap& m,
+                           const cplx<T>* table, cplx<T>* scratch, cplx<T>* grids, cudaStream_t st) {
+  const long ng = (n_fields + 1) / 2;
+  if (ng == 0) return cudaSuccess;
+  cplx<T>* S = scratch;
+  cplx<T>* I1 = S + ng * m.NS;
+  cplx<T>* I2 = I1 + ng * (long)N * m.NC;
+  cudaError_t e = sphere_unpack<T, T>(P, n_fields, n_pw, n_half, m.fpos, m.fneg, S, m.NS, false, false, st);
+  if (e != cudaSuccess) return e;
+  return pruned<T>(true, S, I1, I2, grids, ng, N, m, table, st);
+}
+
+// real-space grids (read only) -> packed fields: scale * sphere values plus the optional
+// diagonal term of sphere_pack; sign -1 transform.
+template <typename T>
+cudaError_t grid_to_sphere(cplx<T>* grids, long n_fields, int n_pw, int n_half, int N, const SphereMap& m,
+                           const cplx<T>* table, cplx<T>* scratch, double scale, T* out, const T* add_in,
+                           const double* g2p, const double* eps, double shift, int n_occ, cudaStream_t st) {
+  const long ng = (n_fields + 1) / 2;
+  if (ng == 0) return cudaSuccess;
+  cplx<T>* S = scratch;
+  cplx<T>* I1 = S + ng * m.NS;
+  cplx<T>* I2 = I1 + ng * (long)N * m.NC;
+  cudaError_t e = pruned<T>(false, S, I1, I2, grids, ng, N, m, table, st);
+  if (e != cudaSuccess) return e;
+  return sphere_pack<T, T>(S, n_fields, n_pw, n_half, m.fpos, m.fneg, m.NS, scale, out, add_in, g2p, eps,
+                           shift, n_occ, st);
+}
+
+template cudaError_t sphere_to_grid<float>(const float*, long, int, int, int, const SphereMap&, const float2*, float2*, float2*, cudaStream_t);
+template cudaError_t sphere_to_grid<double>(const double*, long, int, int, int, const SphereMap&, const double2*, double2*, double2*, cudaStream_t);
+template cudaError_t grid_to_sphere<float>(float2*, long, int, int, int, const SphereMap&, const float2*, float2*, double, float*, const float*, const double*, const double*, double, int, cudaStream_t);
+template cudaError_t grid_to_sphere<double>(double2*, long, int, int, int, const SphereMap&, const double2*, double2*, double, double*, const double*, const double*, const double*, double, int, cudaStream_t);
+
+// Column-ordered sphere from Miller indices (host): +G_k and -G_k (k > 0) sorted by
+// (x slot, y, z) with x slots the sorted distinct x grid indices.
+void build_sphere_map(int N, int n_half, const int* miller, SphereMapHost& h) {
+  auto wrap = [N](int v) { return ((v % N) + N) % N; };
+  struct Pt { int x, y, z, k, neg; };
+  std::vector<Pt> pts;
+  pts.reserve(2 * (size_t)n_half);
+  for (int k = 0; k < n_half; ++k) {
+    const int* q = miller + 3 * k;
+    pts.push_back({wrap(q[0]), wrap(q[1]), wrap(q[2]), k, 0});
+    if (k > 0) pts.push_back({wrap(-q[0]), wrap(-q[1]), wrap(-q[2]), k, 1});
+  }
+  std::sort(pts.begin(), pts.end(), [](const Pt& a, const Pt& b) {
+    if (a.x != b.x) return a.x < b.x;
+    if (a.y != b.y) return a.y < b.y;
+    return a.z < b.z;
+  });
+  h.NS = (int)pts.size();
+  h.fpos.assign(n_half, -1);
+  h.fneg.assign(n_half, -1);
+  h.zs.resize(h.NS);
+  h.jcol.resize(h.NS);
+  h.cstart.clear(); h.cy.clear(); h.cxi.clear(); h.xs.clear(); h.xcol.clear();
+  for (int j = 0; j < h.NS; ++j) {
+    const Pt& p = pts[j];
+    const bool new_x = (j == 0) || p.x != pts[j - 1].x;
+    const bool new_c = new_x || p.y != pts[j - 1].y;
+    if (new_x) { h.xs.push_back(p.x); h.xcol.push_back((int)h.cy.size()); }
+    if (new_c) { h.cstart.push_back(j); h.cy.push_back(p.y); h.cxi.push_back((int)h.xs.size() - 1); }
+    h.zs[j] = p.z;
+    h.jcol[j] = (int)h.cy.size() - 1;
+    (p.neg ? h.fneg : h.fpos)[p.k] = j;
+  }
+  h.NC = (int)h.cy.size();
+  h.NX = (int)h.xs.size();
+  h.cstart.push_back(h.NS);
+  h.xcol.push_back(h.NC);
+  if (h.fneg[0] < 0) h.fneg[0] = h.fpos[0];
+}
 
 bool fft_supported(int N) {
   return N == 16 || N == 32 || N == 48 || N == 64 || N == 72 || N == 96;

@@ -25,6 +25,30 @@ template <typename T>
 cudaError_t grid_coulomb(cplx<T>* grids, long n_grids, int N, double L, double omega, int mode,
                          double scale, cudaStream_t st);
 
+// column-ordered plane-wave sphere for the pruned sphere <-> grid transforms (device
+// arrays; see fft.cu): NS points (+G and -G), NC (x, y) columns, NX distinct x values
+struct SphereMap {
+  int NS = 0, NC = 0, NX = 0;
+  const int *fpos = nullptr, *fneg = nullptr;   // [n_half] sphere position of +G_k, -G_k
+  const int *zs = nullptr, *jcol = nullptr;     // [NS] z index, column of each point
+  const int *cstart = nullptr;                  // [NC + 1] first point of each column
+  const int *cy = nullptr, *cxi = nullptr;      // [NC] y index, x slot of each column
+  const int *xs = nullptr, *xcol = nullptr;     // [NX] x index of each slot, [NX + 1] first column
+};
+struct SphereMapHost {
+  int NS = 0, NC = 0, NX = 0;
+  std::vector<int> fpos, fneg, zs, jcol, cstart, cy, cxi, xs, xcol;
+};
+void build_sphere_map(int N, int n_half, const int* miller, SphereMapHost& h);
+size_t sphere_scratch_per_grid(int N, const SphereMap& m);
+template <typename T>
+cudaError_t sphere_to_grid(const T* P, long n_fields, int n_pw, int n_half, int N, const SphereMap& m,
+                           const cplx<T>* table, cplx<T>* scratch, cplx<T>* grids, cudaStream_t st);
+template <typename T>
+cudaError_t grid_to_sphere(cplx<T>* grids, long n_fields, int n_pw, int n_half, int N, const SphereMap& m,
+                           const cplx<T>* table, cplx<T>* scratch, double scale, T* out, const T* add_in,
+                           const double* g2p, const double* eps, double shift, int n_occ, cudaStream_t st);
+
 // ---- gemm.cu ----
 template <typename T, typename TC>
 cudaError_t gemm(bool at, bool bt, int M, int N, int K, double alpha, const T* A, long lda,
