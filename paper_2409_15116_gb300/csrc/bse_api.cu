@@ -97,6 +97,9 @@ struct bse_ctx {
   int *gpos = nullptr, *gneg = nullptr;
   SphereMap sph;             // column-ordered sphere for the pruned transforms
   double *g2p = nullptr, *eps = nullptr, *f = nullptr;
+  // 1/2|G|^2 per packed coordinate and Delta - eps_v per orbital, in both precisions
+  double *g2h64 = nullptr, *esh64 = nullptr;
+  float *g2h32 = nullptr, *esh32 = nullptr;
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
   // FP64 masters and FP32 copies
@@ -278,6 +281,12 @@ template <> float* pdep_of<float>(bse_ctx* c) { return c->pdep32; }
 template <typename T> T* vloc_of(bse_ctx* c);
 template <> double* vloc_of<double>(bse_ctx* c) { return c->vloc64; }
 template <> float* vloc_of<float>(bse_ctx* c) { return c->vloc32; }
+template <typename T> const T* g2h_of(bse_ctx* c);
+template <> const double* g2h_of<double>(bse_ctx* c) { return c->g2h64; }
+template <> const float* g2h_of<float>(bse_ctx* c) { return c->g2h32; }
+template <typename T> const T* esh_of(bse_ctx* c);
+template <> const double* esh_of<double>(bse_ctx* c) { return c->esh64; }
+template <> const float* esh_of<float>(bse_ctx* c) { return c->esh32; }
 template <typename T> const cplx<T>* tw_of(bse_ctx* c);
 template <> const double2* tw_of<double>(bse_ctx* c) { return c->tw64; }
 template <> const float2* tw_of<float>(bse_ctx* c) { return c->tw32; }
@@ -333,13 +342,14 @@ int ensure_workspace(bse_ctx* c, long n_vec) {
 
 // ---------------------------------------------------------------------------------
 // K1d tile autotuner: at the first application, time every tile variant (points and
-// vectors per CTA) that fits shared memory on the real inputs (twice each, CUDA events on
-// the context stream) and keep the fastest. The choice only changes the tiling, never
-// the summation order.
+// vectors per CTA) that fits shared memory on the real inputs restricted to the first
+// eighth of the grid points (twice each, CUDA events on the context stream) and keep the
+// fastest. The choice only changes the tiling, never the summation order.
 // ---------------------------------------------------------------------------------
 template <typename T>
 int autotune_k1d(bse_ctx* c, int nv, long n3, const T* ga, const T* gh, T* gr, double sf) {
   if (!c->autotune) { c->k1d_sc = k1d_default_variant<T>(c->n_occ); return BSE_OK; }
+  const long n_pts = std::max<long>(TAU_TB, (n3 / 8) / TAU_TB * TAU_TB);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -351,7 +361,7 @@ int autotune_k1d(bse_ctx* c, int nv, long n3, const T* ga, const T* gh, T* gr, d
     for (int rep = 0; rep < 2; ++rep) {
       CK(cudaEventRecord(e0, c->st));
       CK(k1d_tiled<T>(nv, c->n_occ, n3, ga, (const T*)c->tau, c->n_pairs, c->bptr, c->bw, c->bp, c->n_rblocks,
-                      vloc_of<T>(c), gh, upsi_of<T>(c), sf, gr, sc, c->st));
+                      vloc_of<T>(c), gh, upsi_of<T>(c), sf, gr, sc, c->st, n_pts));
       CK(cudaEventRecord(e1, c->st));
       CK(cudaEventSynchronize(e1));
       CK(cudaEventElapsedTime(&t, e0, e1));
@@ -430,7 +440,7 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
       const double gsc = gb * (double)sphere_scratch_per_grid(N, c->sph) / (double)n3;
       Scope sc(c, "fft_forward_r", gb + 2.0 * gsc + 3.0 * nf * c->n_pw * sz, fft_flops(n3, ngr));
       CK(grid_to_sphere<T>(gr, nf, c->n_pw, c->n_half, N, c->sph, tw_of<T>(c), ga, 1.0 / (double)n3, aout,
-                           ain, c->g2p, c->eps, c->scissor, c->n_occ, c->st));
+                           ain, g2h_of<T>(c), esh_of<T>(c), c->n_occ, c->st));
     }
     {
       Scope sc(c, "projector_pc", (3.0 * nf * c->n_pw + (double)c->n_occ * c->n_pw) * sz,
@@ -546,7 +556,7 @@ int build_tau_impl(bse_ctx* c) {
     CK(grid_coulomb<T>(grids, ng, c->N, c->L, c->omega, 1, 1.0 / (double)n3, c->st));
     if (c->n_pdep > 0) {
       CK((sphere_pack<T, T>(grids, b, c->n_pw, c->n_half, c->gpos, c->gneg, n3, 1.0, X, nullptr,
-                            nullptr, nullptr, 0.0, 1, c->st)));
+                            nullptr, nullptr, 1, c->st)));
       bool done = false;
       if constexpr (sizeof(T) == 4) {
         if (c->tc_ok) {
@@ -722,7 +732,7 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
     const int ky = std::min(m, keep);
     {
       Scope sc(c, "davidson_eigh", 8.0 * m * m, 4.0 / 3.0 * m * m * (double)m);
-      CK(eigh_lowest(m, ky, Hs, ms, jw, Yv, theta, info, c->st));
+      CK(eigh_lowest(m, ky, Hs, ms, jw, Yv, theta, info, sizeof(T) == 4, c->st));
     }
     kk = std::min(ne, m);
     {
@@ -776,7 +786,7 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
         if (hb) { diag = true; ++fallbacks; }
       }
       if (diag)
-        CK(precond_diag<T>(nt, c->n_occ, c->n_pw, Rr, theta, which, c->g2p, c->eps, c->v0, c->scissor,
+        CK(precond_diag<T>(nt, c->n_occ, c->n_pw, Rr, theta, which, g2h_of<T>(c), c->eps, c->v0, c->scissor,
                            Tt, c->st));
       CA(proj(nt, Tt));
     }
@@ -1005,6 +1015,16 @@ int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) 
   }
   UPLOAD(c->g2p, c->g2p_h.data(), c->n_pw);
   UPLOAD(c->eps, s->eps, c->n_occ);
+  {
+    std::vector<double> g2h(c->n_pw), esh(c->n_occ);
+    for (int j = 0; j < c->n_pw; ++j) g2h[j] = 0.5 * c->g2p_h[j];
+    for (int v = 0; v < c->n_occ; ++v) esh[v] = c->scissor - s->eps[v];
+    std::vector<float> g2hf(g2h.begin(), g2h.end()), eshf(esh.begin(), esh.end());
+    UPLOAD(c->g2h64, g2h.data(), g2h.size());
+    UPLOAD(c->esh64, esh.data(), esh.size());
+    UPLOAD(c->g2h32, g2hf.data(), g2hf.size());
+    UPLOAD(c->esh32, eshf.data(), eshf.size());
+  }
   UPLOAD(c->f, fh.data(), fh.size());
   UPLOAD(c->psi64, s->psi, npsi);
   UPLOAD(c->vloc64, s->v_loc, c->n3);
@@ -1531,7 +1551,7 @@ int apply_static_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out, unsigned 
                       c->nbr_p, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
   }
   CK(grid_to_sphere<T>(gr, nf, c->n_pw, c->n_half, N, c->sph, tw_of<T>(c), ga, 1.0 / (double)n3, a_out,
-                       a_in, c->g2p, c->eps, c->scissor, c->n_occ, c->st));
+                       a_in, g2h_of<T>(c), esh_of<T>(c), c->n_occ, c->st));
   // P_c with the SIMT GEMM (the tensor-core path would allocate split buffers)
   const T* psi = psi_of<T>(c);
   CK((gemm<T, T>(false, true, (int)nf, c->n_occ, c->n_pw, 1.0, a_out, c->n_pw, psi, c->n_pw, 0.0, cb,

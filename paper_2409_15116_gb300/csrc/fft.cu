@@ -425,7 +425,7 @@ cudaError_t sphere_to_grid(const T* P, long n_fields, int n_pw, int n_half, int 
 template <typename T>
 cudaError_t grid_to_sphere(cplx<T>* grids, long n_fields, int n_pw, int n_half, int N, const SphereMap& m,
                            const cplx<T>* table, cplx<T>* scratch, double scale, T* out, const T* add_in,
-                           const double* g2p, const double* eps, double shift, int n_occ, cudaStream_t st) {
+                           const T* g2h, const T* esh, int n_occ, cudaStream_t st) {
   const long ng = (n_fields + 1) / 2;
   if (ng == 0) return cudaSuccess;
   cplx<T>* S = scratch;
@@ -433,14 +433,14 @@ cudaError_t grid_to_sphere(cplx<T>* grids, long n_fields, int n_pw, int n_half, 
   cplx<T>* I2 = I1 + ng * (long)N * m.NC;
   cudaError_t e = pruned<T>(false, S, I1, I2, grids, ng, N, m, table, st);
   if (e != cudaSuccess) return e;
-  return sphere_pack<T, T>(S, n_fields, n_pw, n_half, m.fpos, m.fneg, m.NS, scale, out, add_in, g2p, eps,
-                           shift, n_occ, st);
+  return sphere_pack<T, T>(S, n_fields, n_pw, n_half, m.fpos, m.fneg, m.NS, scale, out, add_in, g2h, esh,
+                           n_occ, st);
 }
 
 template cudaError_t sphere_to_grid<float>(const float*, long, int, int, int, const SphereMap&, const float2*, float2*, float2*, cudaStream_t);
 template cudaError_t sphere_to_grid<double>(const double*, long, int, int, int, const SphereMap&, const double2*, double2*, double2*, cudaStream_t);
-template cudaError_t grid_to_sphere<float>(float2*, long, int, int, int, const SphereMap&, const float2*, float2*, double, float*, const float*, const double*, const double*, double, int, cudaStream_t);
-template cudaError_t grid_to_sphere<double>(double2*, long, int, int, int, const SphereMap&, const double2*, double2*, double, double*, const double*, const double*, const double*, double, int, cudaStream_t);
+template cudaError_t grid_to_sphere<float>(float2*, long, int, int, int, const SphereMap&, const float2*, float2*, double, float*, const float*, const float*, const float*, int, cudaStream_t);
+template cudaError_t grid_to_sphere<double>(double2*, long, int, int, int, const SphereMap&, const double2*, double2*, double, double*, const double*, const double*, const double*, int, cudaStream_t);
 
 // Column-ordered sphere from Miller indices (host): +G_k and -G_k (k > 0) sorted by
 // (x slot, y, z) with x slots the sorted distinct x grid indices.
@@ -535,14 +535,14 @@ __global__ void sphere_unpack_kernel(const TI* __restrict__ P, long n_fields, in
 }
 
 // packed fields 2c, 2c+1 <- scale * grids[c] on the sphere (Hermitian separation), plus
-// the optional diagonal term (1/2|G|^2 + shift - eps[f % n_occ]) * add_in[f] (Eq. d).
+// the optional diagonal term (g2h[j] + esh[f % n_occ]) * add_in[f] with g2h = 1/2|G|^2 per
+// packed coordinate and esh_v = Delta - eps_v (Eq. d).
 template <typename T, typename TO>
 __global__ void sphere_pack_kernel(const cplx<T>* __restrict__ grids, long n_fields, int n_pw,
                                    int n_half, const int* __restrict__ gpos,
                                    const int* __restrict__ gneg, long n3, double scale,
                                    TO* __restrict__ out, const TO* __restrict__ add_in,
-                                   const double* __restrict__ g2p, const double* __restrict__ eps,
-                                   double shift, int n_occ) {
+                                   const T* __restrict__ g2h, const T* __restrict__ esh, int n_occ) {
   using C = cplx<T>;
   const long n_c = (n_fields + 1) / 2;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -568,17 +568,17 @@ __global__ void sphere_pack_kernel(const cplx<T>* __restrict__ grids, long n_fie
   const long fa = 2 * c, fb = 2 * c + 1;
   const int j0 = 2 * k, j1 = 2 * k + 1;
   if (add_in) {
-    const double ea = eps[fa % n_occ];
-    a0 += (T)((0.5 * g2p[j0] + shift - ea) * (double)add_in[fa * n_pw + j0]);
-    if (k) a1 += (T)((0.5 * g2p[j1] + shift - ea) * (double)add_in[fa * n_pw + j1]);
+    const T ea = esh[fa % n_occ];
+    a0 += (g2h[j0] + ea) * (T)add_in[fa * n_pw + j0];
+    if (k) a1 += (g2h[j1] + ea) * (T)add_in[fa * n_pw + j1];
   }
   out[fa * n_pw + j0] = (TO)a0;
   out[fa * n_pw + j1] = (TO)a1;
   if (fb < n_fields) {
     if (add_in) {
-      const double eb = eps[fb % n_occ];
-      b0 += (T)((0.5 * g2p[j0] + shift - eb) * (double)add_in[fb * n_pw + j0]);
-      if (k) b1 += (T)((0.5 * g2p[j1] + shift - eb) * (double)add_in[fb * n_pw + j1]);
+      const T eb = esh[fb % n_occ];
+      b0 += (g2h[j0] + eb) * (T)add_in[fb * n_pw + j0];
+      if (k) b1 += (g2h[j1] + eb) * (T)add_in[fb * n_pw + j1];
     }
     out[fb * n_pw + j0] = (TO)b0;
     out[fb * n_pw + j1] = (TO)b1;
@@ -605,21 +605,20 @@ cudaError_t sphere_unpack(const TI* P, long n_fields, int n_pw, int n_half, cons
 template <typename T, typename TO>
 cudaError_t sphere_pack(const cplx<T>* grids, long n_fields, int n_pw, int n_half, const int* gpos,
                         const int* gneg, long n3, double scale, TO* out, const TO* add_in,
-                        const double* g2p, const double* eps, double shift, int n_occ,
-                        cudaStream_t st) {
+                        const T* g2h, const T* esh, int n_occ, cudaStream_t st) {
   const long n_c = (n_fields + 1) / 2;
   if (n_c == 0) return cudaSuccess;
   dim3 grid((unsigned)((n_half + 255) / 256), (unsigned)(n_c < 65535 ? n_c : 65535));
   sphere_pack_kernel<T, TO><<<grid, 256, 0, st>>>(
-      grids, n_fields, n_pw, n_half, gpos, gneg, n3, scale, out, add_in, g2p, eps, shift, n_occ); note_launch();
+      grids, n_fields, n_pw, n_half, gpos, gneg, n3, scale, out, add_in, g2h, esh, n_occ); note_launch();
   return cudaGetLastError();
 }
 
 template cudaError_t sphere_unpack<double, double>(const double*, long, int, int, const int*, const int*, double2*, long, bool, bool, cudaStream_t);
 template cudaError_t sphere_unpack<float, float>(const float*, long, int, int, const int*, const int*, float2*, long, bool, bool, cudaStream_t);
 template cudaError_t sphere_unpack<float, double>(const double*, long, int, int, const int*, const int*, float2*, long, bool, bool, cudaStream_t);
-template cudaError_t sphere_pack<double, double>(const double2*, long, int, int, const int*, const int*, long, double, double*, const double*, const double*, const double*, double, int, cudaStream_t);
-template cudaError_t sphere_pack<float, float>(const float2*, long, int, int, const int*, const int*, long, double, float*, const float*, const double*, const double*, double, int, cudaStream_t);
+template cudaError_t sphere_pack<double, double>(const double2*, long, int, int, const int*, const int*, long, double, double*, const double*, const double*, const double*, int, cudaStream_t);
+template cudaError_t sphere_pack<float, float>(const float2*, long, int, int, const int*, const int*, long, double, float*, const float*, const float*, const float*, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------------
 // multiply complex grids by a real, even function of |G| (keeps field pairs separable)
@@ -632,6 +631,7 @@ __global__ void grid_coulomb_kernel(cplx<T>* __restrict__ grids, long n_grids, i
   const int n3 = N * N * N;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n3) return;
+  // the factor depends on the point only: computed once, then applied to a stride of grids
   const int x = r % N, y = (r / N) % N, z = r / (N * N);
   const int nx = x < N / 2 ? x : x - N, ny = y < N / 2 ? y : y - N, nz = z < N / 2 ? z : z - N;
   const double g = 6.283185307179586476925286766559 / L;
@@ -639,10 +639,10 @@ __global__ void grid_coulomb_kernel(cplx<T>* __restrict__ grids, long n_grids, i
   double f = 0.0;
   if (g2 > 0) f = (mode == 0) ? 12.566370614359172953850573533118 / (g2 * omega)
                               : 3.5449077018110320545963349666823 / sqrt(g2);
-  f *= scale;
+  const T ft = (T)(f * scale);
   for (long b = blockIdx.y; b < n_grids; b += gridDim.y) {
     cplx<T> v = grids[b * n3 + r];
-    v.x = (T)(v.x * f); v.y = (T)(v.y * f);
+    v.x *= ft; v.y *= ft;
     grids[b * n3 + r] = v;
   }
 }
@@ -652,9 +652,8 @@ cudaError_t grid_coulomb(cplx<T>* grids, long n_grids, int N, double L, double o
                          double scale, cudaStream_t st) {
   if (n_grids == 0) return cudaSuccess;
   const long n3 = (long)N * N * N;
-  dim3 grid((unsigned)((n3 + 255) / 256), (unsigned)(n_grids < 65535 ? n_grids : 65535));
-  grid_coulomb_kernel<T><<<grid, 256, 0, st>>>(grids, n_grids, N, L,
-                                                                         omega, mode, scale); note_launch();
+  dim3 grid((unsigned)((n3 + 255) / 256), (unsigned)(n_grids < 8 ? n_grids : 8));
+  grid_coulomb_kernel<T><<<grid, 256, 0, st>>>(grids, n_grids, N, L, omega, mode, scale); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t grid_coulomb<float>(float2*, long, int, double, double, int, double, cudaStream_t);

@@ -228,7 +228,7 @@ size_t variant_smem(int n_occ, int v) {
 template <typename T, int TR, int SC>
 cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T* tau, long n_pairs, const int* bptr,
                        const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
-                       const T* upsi, double sf, T* out, cudaStream_t st) {
+                       const T* upsi, double sf, T* out, long n_pts, cudaStream_t st) {
   static_assert(K1D_THREADS % TR == 0 && 32 % TR == 0 && K1D_THREADS / TR >= SC, "tile shape");
   if constexpr (sizeof(T) == 8 && SC == 8) {
     return cudaErrorInvalidValue;   // 64 double accumulators per lane do not fit the register budget
@@ -241,7 +241,7 @@ cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T* tau, 
                                   (int)K1D_SMEM_MAX);
     });
     if (e0 != cudaSuccess) return e0;
-    const long blocks = (n3 / TR) * ((n_vec + SC - 1) / SC);
+    const long blocks = (n_pts / TR) * ((n_vec + SC - 1) / SC);
     k1d_tile_kernel<T, TR, SC><<<(unsigned)blocks, K1D_THREADS, smem, st>>>(
         n_vec, n_occ, n3, a, tau, n_pairs, bptr, bw, bp, n_blocks, vloc, vh, upsi, (T)sf, out);
     note_launch();
@@ -275,15 +275,17 @@ int k1d_default_variant(int n_occ) {
 template <typename T>
 cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, long n_pairs, const int* bptr,
                       const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
-                      const T* upsi, double sf, T* out, int variant, cudaStream_t st) {
+                      const T* upsi, double sf, T* out, int variant, cudaStream_t st, long n_pts) {
   if (n_vec <= 0) return cudaSuccess;
+  if (n_pts < 0) n_pts = n3;
+  if (n_pts > n3 || n_pts % TAU_TB) return cudaErrorInvalidValue;
   if (variant == 0) variant = k1d_default_variant<T>(n_occ);
   if (!k1d_fits<T>(n_occ, variant)) return cudaErrorInvalidValue;
   if (n3 % TAU_TB || TAU_TB % kVariants[variant].tr) return cudaErrorInvalidValue;
 #define BSE_K1D_CASE(V, TR, SC)                                                                      \
   case V:                                                                                            \
     return launch_k1d<T, TR, SC>(n_vec, n_occ, n3, a, tau, n_pairs, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, \
-                                 out, st);
+                                 out, n_pts, st);
   switch (variant) {
     BSE_K1D_CASE(1, 16, 8)
     BSE_K1D_CASE(2, 8, 8)
@@ -296,8 +298,8 @@ cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, l
 #undef BSE_K1D_CASE
 }
 
-template cudaError_t k1d_tiled<float>(int, int, long, const float*, const float*, long, const int*, const int*, const int4*, int, const float*, const float*, const float*, double, float*, int, cudaStream_t);
-template cudaError_t k1d_tiled<double>(int, int, long, const double*, const double*, long, const int*, const int*, const int4*, int, const double*, const double*, const double*, double, double*, int, cudaStream_t);
+template cudaError_t k1d_tiled<float>(int, int, long, const float*, const float*, long, const int*, const int*, const int4*, int, const float*, const float*, const float*, double, float*, int, cudaStream_t, long);
+template cudaError_t k1d_tiled<double>(int, int, long, const double*, const double*, long, const int*, const int*, const int4*, int, const double*, const double*, const double*, double, double*, int, cudaStream_t, long);
 template bool k1d_fits<float>(int, int);
 template bool k1d_fits<double>(int, int);
 template int k1d_default_variant<float>(int);

@@ -16,11 +16,12 @@ template <typename T, typename TI>
 cudaError_t sphere_unpack(const TI* P, long n_fields, int n_pw, int n_half, const int* gpos,
                           const int* gneg, cplx<T>* grids, long n3, bool zero_first,
                           bool accumulate, cudaStream_t st);
+// g2h: 1/2|G|^2 per packed coordinate; esh: Delta - eps_v per orbital (both may be null
+// when add_in is)
 template <typename T, typename TO>
 cudaError_t sphere_pack(const cplx<T>* grids, long n_fields, int n_pw, int n_half, const int* gpos,
                         const int* gneg, long n3, double scale, TO* out, const TO* add_in,
-                        const double* g2p, const double* eps, double shift, int n_occ,
-                        cudaStream_t st);
+                        const T* g2h, const T* esh, int n_occ, cudaStream_t st);
 template <typename T>
 cudaError_t grid_coulomb(cplx<T>* grids, long n_grids, int N, double L, double omega, int mode,
                          double scale, cudaStream_t st);
@@ -47,7 +48,7 @@ cudaError_t sphere_to_grid(const T* P, long n_fields, int n_pw, int n_half, int 
 template <typename T>
 cudaError_t grid_to_sphere(cplx<T>* grids, long n_fields, int n_pw, int n_half, int N, const SphereMap& m,
                            const cplx<T>* table, cplx<T>* scratch, double scale, T* out, const T* add_in,
-                           const double* g2p, const double* eps, double shift, int n_occ, cudaStream_t st);
+                           const T* g2h, const T* esh, int n_occ, cudaStream_t st);
 
 // ---- gemm.cu ----
 template <typename T, typename TC>
@@ -122,7 +123,7 @@ bool k1d_fits(int n_occ, int variant);
 template <typename T>
 cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, long n_pairs, const int* bptr,
                       const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
-                      const T* upsi, double sf, T* out, int variant, cudaStream_t st);
+                      const T* upsi, double sf, T* out, int variant, cudaStream_t st, long n_pts = -1);
 template <typename T>
 cudaError_t scale_columns(int rows, int cols, T* C, long ldc, const double* f, cudaStream_t st);
 template <typename TI, typename TO>
@@ -136,7 +137,7 @@ template <typename T>
 cudaError_t row_norms2(int k, long dim, const T* X, double* norms2, cudaStream_t st);
 template <typename T>
 cudaError_t precond_diag(int k, int n_occ, int n_pw, const T* R, const double* theta,
-                         const int* which, const double* g2p, const double* eps, double v0,
+                         const int* which, const T* g2h, const double* eps, double v0,
                          double shift, T* out, cudaStream_t st);
 template <typename T>
 cudaError_t zero_pad_column(int rows, int n_pw, T* X, cudaStream_t st);
@@ -147,7 +148,7 @@ cudaError_t set_unit(T* x, long dim, long idx, cudaStream_t st);
 cudaError_t symmetrize(int m, double* A, long lda, cudaStream_t st);
 cudaError_t mirror_new(double* A, long lda, int m0, int m1, cudaStream_t st);
 cudaError_t eigh_lowest(int m, int k, const double* A, long lda, double* work, double* V, double* w,
-                        int* info, cudaStream_t st);
+                        int* info, bool single, cudaStream_t st);
 cudaError_t cholesky_inverse(int b, const double* S, long lds, double* Linv, int* info,
                              cudaStream_t st);
 bool finite_check_host(const double* x, long n);

@@ -101,23 +101,34 @@ cudaError_t normalize_overlap(int n, double* gram, double* diag, cudaStream_t st
 // ---------------------------------------------------------------------------------
 // Hartree pair density of Eq. (k1e): h_s(r) = sum_w u_psi_w(r) u_a_sw(r)
 // ---------------------------------------------------------------------------------
-template <typename T>
+template <typename T, int SV>
 __global__ void hartree_density_kernel(int n_vec, int n_occ, long n3, const T* __restrict__ a,
                                        const T* __restrict__ upsi, T* __restrict__ h) {
+  // SV vectors per thread, so each psi_w(r) is read once per SV vectors
   const long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
+  const int s0 = blockIdx.y * SV;
   if (r >= n3) return;
-  T acc = 0;
-  const long f0 = (long)s * n_occ;
-  for (int w = 0; w < n_occ; ++w) acc += upsi[pair_off<T>(w, r, n3)] * a[pair_off<T>(f0 + w, r, n3)];
-  h[pair_off<T>(s, r, n3)] = acc;
+  const int ns = min(SV, n_vec - s0);
+  T acc[SV];
+#pragma unroll
+  for (int q = 0; q < SV; ++q) acc[q] = 0;
+  for (int w = 0; w < n_occ; ++w) {
+    const T u = upsi[pair_off<T>(w, r, n3)];
+#pragma unroll
+    for (int q = 0; q < SV; ++q)
+      if (q < ns) acc[q] += u * a[pair_off<T>((long)(s0 + q) * n_occ + w, r, n3)];
+  }
+#pragma unroll
+  for (int q = 0; q < SV; ++q)
+    if (q < ns) h[pair_off<T>(s0 + q, r, n3)] = acc[q];
 }
 template <typename T>
 cudaError_t hartree_density(int n_vec, int n_occ, long n3, const T* a, const T* upsi, T* h,
                             cudaStream_t st) {
   if (!n_vec) return cudaSuccess;
-  dim3 grid(nblk(n3), n_vec);
-  hartree_density_kernel<T><<<grid, 256, 0, st>>>(n_vec, n_occ, n3, a, upsi, h); note_launch();
+  constexpr int SV = 8;
+  dim3 grid(nblk(n3), (n_vec + SV - 1) / SV);
+  hartree_density_kernel<T, SV><<<grid, 256, 0, st>>>(n_vec, n_occ, n3, a, upsi, h); note_launch();
   return cudaGetLastError();
 }
 
@@ -231,21 +242,22 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return v;
 }
 
-// R_i = LX_i - theta_i X_i and ||R_i||^2 (FP64 accumulation)
+// R_i = LX_i - theta_i X_i and ||R_i||^2. Arithmetic in the data precision (per-thread
+// partial sums of a few dozen terms), block and grid sums in double.
 template <typename T>
 __global__ void residual_kernel(long dim, const T* X, const T* LX, const double* theta, T* R,
                                 double* norms2) {
   __shared__ double sh[32];
   const int i = blockIdx.y;
-  const double th = theta[i];
-  double acc = 0;
+  const T th = (T)theta[i];
+  T acc = 0;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < dim; e += (long)gridDim.x * blockDim.x) {
-    const double r = (double)LX[i * dim + e] - th * (double)X[i * dim + e];
-    R[i * dim + e] = (T)r;
-    acc += r * r;
+    const T r = fma(-th, X[i * dim + e], LX[i * dim + e]);
+    R[i * dim + e] = r;
+    acc = fma(r, r, acc);
   }
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) atomicAdd(norms2 + i, acc);
+  const double tot = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) atomicAdd(norms2 + i, tot);
 }
 template <typename T>
 cudaError_t residuals(int k, long dim, const T* X, const T* LX, const double* theta, T* R,
@@ -263,13 +275,13 @@ template <typename T>
 __global__ void row_norms2_kernel(long dim, const T* X, double* norms2) {
   __shared__ double sh[32];
   const int i = blockIdx.y;
-  double acc = 0;
+  T acc = 0;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < dim; e += (long)gridDim.x * blockDim.x) {
-    const double x = (double)X[i * dim + e];
-    acc += x * x;
+    const T x = X[i * dim + e];
+    acc = fma(x, x, acc);
   }
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) atomicAdd(norms2 + i, acc);
+  const double tot = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) atomicAdd(norms2 + i, tot);
 }
 template <typename T>
 cudaError_t row_norms2(int k, long dim, const T* X, double* norms2, cudaStream_t st) {
@@ -287,25 +299,27 @@ cudaError_t row_norms2(int k, long dim, const T* X, double* norms2, cudaStream_t
 // diagonal carries no information about L - theta. The pad coordinate is set to 0.
 template <typename T>
 __global__ void precond_diag_kernel(int n_occ, int n_pw, const T* R, const double* theta,
-                                    const int* which, const double* g2p, const double* eps,
+                                    const int* which, const T* g2h, const double* eps,
                                     double v0, double shift, T* out) {
   const long dim = (long)n_occ * n_pw;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = blockIdx.y, t = blockIdx.z;
   if (j >= n_pw) return;
   const int i = which[t];
-  double den = 0.5 * g2p[j] + v0 + shift - eps[v] - theta[i];
-  if (den < 0.1) den = 0.1;
+  // d - theta = 1/2|G|^2 + (V(0) + Delta - eps_v - theta); the bracket is one value per block
+  const T c = (T)(v0 + shift - eps[v] - theta[i]);
+  T den = g2h[j] + c;
+  if (den < (T)0.1) den = (T)0.1;
   const long e = (long)v * n_pw + j;
-  out[t * dim + e] = (j == 1) ? (T)0 : (T)((double)R[(long)i * dim + e] / den);
+  out[t * dim + e] = (j == 1) ? (T)0 : R[(long)i * dim + e] / den;
 }
 template <typename T>
 cudaError_t precond_diag(int k, int n_occ, int n_pw, const T* R, const double* theta,
-                         const int* which, const double* g2p, const double* eps, double v0,
+                         const int* which, const T* g2h, const double* eps, double v0,
                          double shift, T* out, cudaStream_t st) {
   if (!k) return cudaSuccess;
   dim3 grid(nblk(n_pw), n_occ, k);
-  precond_diag_kernel<T><<<grid, 256, 0, st>>>(n_occ, n_pw, R, theta, which, g2p, eps, v0, shift, out); note_launch();
+  precond_diag_kernel<T><<<grid, 256, 0, st>>>(n_occ, n_pw, R, theta, which, g2h, eps, v0, shift, out); note_launch();
   return cudaGetLastError();
 }
 
@@ -324,9 +338,9 @@ cudaError_t zero_pad_column(int rows, int n_pw, T* X, cudaStream_t st) {
 template <typename T>
 __global__ void scale_rows_kernel(long dim, T* X, const double* s) {
   const int i = blockIdx.y;
-  const double f = s[i];
+  const T f = (T)s[i];
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < dim; e += (long)gridDim.x * blockDim.x)
-    X[i * dim + e] = (T)((double)X[i * dim + e] * f);
+    X[i * dim + e] *= f;
 }
 template <typename T>
 cudaError_t scale_rows(int k, long dim, T* X, const double* s, cudaStream_t st) {
@@ -475,7 +489,7 @@ bool finite_check_host(const double* x, long n) {
                                     cudaStream_t);                                                 \
   template cudaError_t row_norms2<T>(int, long, const T*, double*, cudaStream_t);                  \
   template cudaError_t precond_diag<T>(int, int, int, const T*, const double*, const int*,         \
-                                       const double*, const double*, double, double, T*,           \
+                                       const T*, const double*, double, double, T*,                \
                                        cudaStream_t);                                              \
   template cudaError_t zero_pad_column<T>(int, int, T*, cudaStream_t);                             \
   template cudaError_t scale_rows<T>(int, long, T*, const double*, cudaStream_t);                  \
