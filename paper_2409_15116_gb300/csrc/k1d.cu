@@ -26,7 +26,6 @@ namespace bse {
 
 namespace {
 
-constexpr int K1D_THREADS = 256;
 constexpr int K1D_PD = 8;                       // tau prefetch depth (entries per lane)
 constexpr size_t K1D_SMEM_MAX = 220 * 1024;     // opt-in dynamic shared memory used at most
 
@@ -55,6 +54,32 @@ __device__ __forceinline__ void lds_vec(T (&v)[SC], const T* p) {
   }
 }
 
+// Staged a(r) layout [w][s / CH][t][CH] with CH = 16 bytes of values: the CH values of one
+// (orbital, point) chunk are one 16-byte load, and the eight lanes of a quarter-warp (eight
+// consecutive points) read 128 contiguous bytes, free of bank conflicts.
+template <typename T, int SC>
+struct ALayout {
+  static constexpr int CH = (SC * (int)sizeof(T) >= 16) ? 16 / (int)sizeof(T) : SC;
+  static constexpr int NCH = SC / CH;
+  // offset of chunk 0 of (w, t) given TR points per tile; chunk c is at + c * TR * CH
+  template <int TR>
+  __device__ __forceinline__ static size_t base(int w, int t) { return ((size_t)w * NCH * TR + t) * CH; }
+};
+
+// SC values of one (orbital, point) of the staged layout
+template <typename T, int SC, int TR>
+__device__ __forceinline__ void lds_a(T (&v)[SC], const T* A, int w, int t) {
+  using L = ALayout<T, SC>;
+  const T* p = A + L::template base<TR>(w, t);
+#pragma unroll
+  for (int c = 0; c < L::NCH; ++c) {
+    T tmp[L::CH];
+    lds_vec<T, L::CH>(tmp, p + (size_t)c * TR * L::CH);
+#pragma unroll
+    for (int q = 0; q < L::CH; ++q) v[c * L::CH + q] = tmp[q];
+  }
+}
+
 // accumulators of one lane: four rows x SC vectors
 template <typename T, int SC, bool PACKED = (sizeof(T) == 4 && SC % 2 == 0)>
 struct RowAcc {
@@ -65,9 +90,7 @@ struct RowAcc {
 #pragma unroll
       for (int s = 0; s < SC; ++s) acc[i][s] = (T)0;
   }
-  __device__ __forceinline__ void mac(const T (&tv)[4], const T* Aw) {
-    T av[SC];
-    lds_vec<T, SC>(av, Aw);
+  __device__ __forceinline__ void mac(const T (&tv)[4], const T (&av)[SC]) {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -85,9 +108,7 @@ struct RowAcc<float, SC, true> {
 #pragma unroll
       for (int j = 0; j < SC / 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
   }
-  __device__ __forceinline__ void mac(const float (&tv)[4], const float* Aw) {
-    float av[SC];
-    lds_vec<float, SC>(av, Aw);
+  __device__ __forceinline__ void mac(const float (&tv)[4], const float (&av)[SC]) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const float2 ti = make_float2(tv[i], tv[i]);
@@ -103,8 +124,8 @@ struct RowAcc<float, SC, true> {
 template <int TR>
 __device__ __forceinline__ int gshfl(unsigned mask, int v, int j) { return __shfl_sync(mask, v, j, TR); }
 
-template <typename T, int TR, int SC>
-__global__ void __launch_bounds__(K1D_THREADS, 2) k1d_tile_kernel(
+template <typename T, int TR, int SC, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k1d_tile_kernel(
     int n_vec, int n_occ, long n3, const T* __restrict__ a, const T* __restrict__ tau, long n_pairs,
     const int* __restrict__ bptr, const int* __restrict__ bw, const int4* __restrict__ bp,
     int n_blocks, const T* __restrict__ vloc, const T* __restrict__ vh,
@@ -113,7 +134,7 @@ __global__ void __launch_bounds__(K1D_THREADS, 2) k1d_tile_kernel(
   constexpr int PD0 = (sizeof(T) == 8) ? K1D_PD / 2 : K1D_PD;
   constexpr int PD = (PD0 < TR) ? PD0 : TR;
   extern __shared__ __align__(16) unsigned char k1d_smem[];
-  T* A = reinterpret_cast<T*>(k1d_smem);            // [n_occ][TR][SC]
+  T* A = reinterpret_cast<T*>(k1d_smem);            // [n_occ][SC / CH][TR][CH]
   T* VH = A + (size_t)n_occ * TR * SC;               // [TR][SC]
   const int n_sc = (n_vec + SC - 1) / SC;
   const int chunk = blockIdx.x % n_sc;
@@ -122,14 +143,17 @@ __global__ void __launch_bounds__(K1D_THREADS, 2) k1d_tile_kernel(
   const int ns = min(SC, n_vec - s0);
   const int tid = threadIdx.x;
   const int t = tid % TR, g = tid / TR;
-  constexpr int G = K1D_THREADS / TR;
+  constexpr int G = NT / TR;
   const long r = r0 + t;
-  // stage a(field (s0+s, w), r0+t) -> A[w][t][s]: item (w, t, s) with s fastest, so the
-  // lanes of a warp fill consecutive shared-memory words
+  // stage a(field (s0+s, w), r0+t) in layout order, so the lanes of a warp fill
+  // consecutive shared-memory words
   {
+    using L = ALayout<T, SC>;
     const int n_items = n_occ * TR * SC;
-    for (int it = tid; it < n_items; it += K1D_THREADS) {
-      const int s = it % SC, tt = (it / SC) % TR, w = it / (SC * TR);
+    for (int it = tid; it < n_items; it += NT) {
+      const int q = it % L::CH, tt = (it / L::CH) % TR, c = (it / (L::CH * TR)) % L::NCH;
+      const int w = it / (SC * TR);
+      const int s = c * L::CH + q;
       if (s < ns)
         cp_async<sizeof(T)>(A + it, a + pair_off<T>((long)(s0 + s) * n_occ + w, r0 + tt, n3));
     }
@@ -177,7 +201,9 @@ __global__ void __launch_bounds__(K1D_THREADS, 2) k1d_tile_kernel(
       for (int d = 0; d < TR; ++d) {
         if (base + d >= e1) break;
         const int sl = d % PD;
-        acc.mac(tq[sl], A + ((size_t)wq[sl] * TR + t) * SC);
+        T av[SC];
+        lds_a<T, SC, TR>(av, A, wq[sl], t);
+        acc.mac(tq[sl], av);
         // refill the slot with entry base + d + PD (index from batch A or B)
         const int j = d + PD;
         int px, py, pz, pw, w;
@@ -202,7 +228,7 @@ __global__ void __launch_bounds__(K1D_THREADS, 2) k1d_tile_kernel(
       if (v >= n_occ) break;
       const T up = sf * upsi[pair_off<T>(v, r, n3)];
       T av[SC], hv[SC];
-      lds_vec<T, SC>(av, A + ((size_t)v * TR + t) * SC);
+      lds_a<T, SC, TR>(av, A, v, t);
       lds_vec<T, SC>(hv, VH + t * SC);
 #pragma unroll
       for (int s = 0; s < SC; ++s) {
@@ -214,9 +240,10 @@ __global__ void __launch_bounds__(K1D_THREADS, 2) k1d_tile_kernel(
   }
 }
 
-// tile variants: (points per CTA, vectors per CTA)
-struct Variant { int tr, sc; };
-constexpr Variant kVariants[] = {{0, 0}, {16, 8}, {8, 8}, {16, 4}, {8, 4}, {16, 2}, {16, 1}};
+// tile variants: (points per CTA, vectors per CTA, threads per CTA)
+struct Variant { int tr, sc, nt; };
+constexpr Variant kVariants[] = {{0, 0, 0}, {16, 8, 512}, {8, 8, 256}, {16, 4, 256}, {8, 4, 256},
+                                 {16, 2, 256}, {16, 1, 256}, {16, 8, 256}, {8, 8, 512}};
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0])) - 1;
 
 template <typename T>
@@ -225,11 +252,11 @@ size_t variant_smem(int n_occ, int v) {
   return ((size_t)n_occ * q.tr * q.sc + (size_t)q.tr * q.sc) * sizeof(T);
 }
 
-template <typename T, int TR, int SC>
+template <typename T, int TR, int SC, int NT>
 cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T* tau, long n_pairs, const int* bptr,
                        const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
                        const T* upsi, double sf, T* out, long n_pts, cudaStream_t st) {
-  static_assert(K1D_THREADS % TR == 0 && 32 % TR == 0 && K1D_THREADS / TR >= SC, "tile shape");
+  static_assert(NT % TR == 0 && 32 % TR == 0 && NT / TR >= SC, "tile shape");
   if constexpr (sizeof(T) == 8 && SC == 8) {
     return cudaErrorInvalidValue;   // 64 double accumulators per lane do not fit the register budget
   } else {
@@ -237,12 +264,12 @@ cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T* tau, 
     static std::once_flag once;
     static cudaError_t once_st = cudaSuccess;
     cudaError_t e0 = once_status(once, once_st, [&] {
-      return cudaFuncSetAttribute(k1d_tile_kernel<T, TR, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      return cudaFuncSetAttribute(k1d_tile_kernel<T, TR, SC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)K1D_SMEM_MAX);
     });
     if (e0 != cudaSuccess) return e0;
     const long blocks = (n_pts / TR) * ((n_vec + SC - 1) / SC);
-    k1d_tile_kernel<T, TR, SC><<<(unsigned)blocks, K1D_THREADS, smem, st>>>(
+    k1d_tile_kernel<T, TR, SC, NT><<<(unsigned)blocks, NT, smem, st>>>(
         n_vec, n_occ, n3, a, tau, n_pairs, bptr, bw, bp, n_blocks, vloc, vh, upsi, (T)sf, out);
     note_launch();
     return cudaGetLastError();
@@ -282,17 +309,19 @@ cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, l
   if (variant == 0) variant = k1d_default_variant<T>(n_occ);
   if (!k1d_fits<T>(n_occ, variant)) return cudaErrorInvalidValue;
   if (n3 % TAU_TB || TAU_TB % kVariants[variant].tr) return cudaErrorInvalidValue;
-#define BSE_K1D_CASE(V, TR, SC)                                                                      \
+#define BSE_K1D_CASE(V, TR, SC, NT)                                                                  \
   case V:                                                                                            \
-    return launch_k1d<T, TR, SC>(n_vec, n_occ, n3, a, tau, n_pairs, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, \
+    return launch_k1d<T, TR, SC, NT>(n_vec, n_occ, n3, a, tau, n_pairs, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, \
                                  out, n_pts, st);
   switch (variant) {
-    BSE_K1D_CASE(1, 16, 8)
-    BSE_K1D_CASE(2, 8, 8)
-    BSE_K1D_CASE(3, 16, 4)
-    BSE_K1D_CASE(4, 8, 4)
-    BSE_K1D_CASE(5, 16, 2)
-    BSE_K1D_CASE(6, 16, 1)
+    BSE_K1D_CASE(1, 16, 8, 512)
+    BSE_K1D_CASE(2, 8, 8, 256)
+    BSE_K1D_CASE(3, 16, 4, 256)
+    BSE_K1D_CASE(4, 8, 4, 256)
+    BSE_K1D_CASE(5, 16, 2, 256)
+    BSE_K1D_CASE(6, 16, 1, 256)
+    BSE_K1D_CASE(7, 16, 8, 256)
+    BSE_K1D_CASE(8, 8, 8, 512)
     default: return cudaErrorInvalidValue;
   }
 #undef BSE_K1D_CASE
