@@ -130,3 +130,30 @@ def test_localized_davidson_vs_oracle_davidson(prec, tol):
     c = ctx_for(inst, prec)
     om, _ = c.davidson(4, 8, 32, res_tol=1e-6 if prec == 0 else 1e-4)
     assert np.abs(om - ref).max() <= tol, (om - ref)
+
+
+# ---------------------------------------------------------------------------------
+# every K1d tile variant (points x vectors per CTA, threads per CTA), fixed through
+# BSE_K1D_VARIANT at context creation, on a ragged block: 11 vectors (partial vector
+# chunks for every chunk size) of an odd N_occ
+# ---------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def ragged_case():
+    inst = make_localized(3, 20.0 * 32 / 72, 32, 13, 2.5, 26, n_eig=4, block=4)
+    Lop = liouville.Liouville(inst)
+    rng = np.random.default_rng(17)
+    A = Lop.project(rng.standard_normal((11, inst.n_occ, inst.n_pw)))
+    return inst, A, Lop.apply(A)
+
+
+@pytest.mark.parametrize("variant", range(1, 9))
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
+def test_k1d_tile_variants_vs_matrix_free(ragged_case, variant, prec, tol, monkeypatch):
+    inst, A, ref = ragged_case
+    monkeypatch.setenv("BSE_K1D_VARIANT", str(variant))
+    c = ctx_for(inst, prec)
+    a = dev(A, prec)
+    out = torch.empty_like(a)
+    c.apply(a, out)
+    got = out.double().cpu().numpy()
+    assert rel(got, ref) <= tol, (variant, rel(got, ref))
