@@ -807,14 +807,23 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
     std::vector<double> n0(nt), n1(nt);
     CK(row_norms2<T>(nt, dim, Tt, nrm, c->st));
     CK(cudaMemcpyAsync(n0.data(), nrm, sizeof(double) * nt, cudaMemcpyDeviceToHost, c->st));
+    // second pass only where the first removed more than half of a direction's squared
+    // norm (the Daniel-Gragg-Kaufman-Stewart test with eta = 1/sqrt 2): without that much
+    // cancellation one pass already leaves the rounding level of the data
+    bool cancelled = false;
     for (int pass = 0; pass < 2; ++pass) {
       CK((gemm<T, double>(false, true, m, nt, (int)dim, 1.0, V, dim, Tt, dim, 0.0, Cm, nt, 0, c->st)));
       CK((convert<double, T>((long)m * nt, Cm, Cmt, c->st)));
       CK((gemm<T, T>(true, false, nt, (int)dim, m, -1.0, Cmt, nt, V, dim, 1.0, Tt, dim, 1, c->st)));
+      CK(row_norms2<T>(nt, dim, Tt, nrm, c->st));
+      CK(cudaMemcpyAsync(n1.data(), nrm, sizeof(double) * nt, cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      if (pass == 0) {
+        for (int t = 0; t < nt; ++t)
+          if (n1[t] < 0.5 * n0[t]) cancelled = true;
+        if (!cancelled) break;
+      }
     }
-    CK(row_norms2<T>(nt, dim, Tt, nrm, c->st));
-    CK(cudaMemcpyAsync(n1.data(), nrm, sizeof(double) * nt, cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
     {
       // A direction that lost all but drop_tol of its norm is rounding noise of the
       // projection and orthogonalisation, not a search direction: in the mixed path the
@@ -833,9 +842,10 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
       nt = w;
     }
     if (nt == 0) break;
-    // mixed path: project the kept directions once more so their occupied-space
-    // leakage is relative to their own (post-orthogonalisation) norm
-    if (sizeof(T) == 4) CA(proj(nt, Tt));
+    // mixed path: where a direction lost more than half its squared norm, project the kept
+    // directions once more so their occupied-space leakage is relative to their own
+    // (post-orthogonalisation) norm
+    if (sizeof(T) == 4 && cancelled) CA(proj(nt, Tt));
     // CholQR2 among the new directions; a failing pivot drops that direction
     for (int pass = 0; pass < 2; ++pass) {
       while (true) {

@@ -177,12 +177,12 @@ namespace {
 
 constexpr int TS_KS = 2048;    // K per CTA (ts_tn)
 constexpr int TS_KC = 32;      // K per staged chunk
-constexpr int TS_BM = 64;      // rows of A per CTA
 constexpr int TS_STAGES = 4;
 
-// staged chunk row: 32 floats in eight 16-byte groups, group g stored at g ^ (row/8 % 8),
-// so that lanes reading the same group of eight different rows hit distinct banks
-__device__ __forceinline__ int ts_off(int row, int g) { return row * TS_KC + ((g ^ ((row >> 3) & 7)) << 2); }
+// staged chunk row: 32 floats in eight 16-byte groups, group g stored at g ^ (row >> SWS) % 8,
+// so that lanes reading the same group of different rows hit distinct banks
+template <int SWS>
+__device__ __forceinline__ int ts_off(int row, int g) { return row * TS_KC + ((g ^ ((row >> SWS) & 7)) << 2); }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -190,37 +190,44 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool va
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
 }
 
+// BM rows of A per CTA (64 or 32); SYM: B is A (a Gram matrix, M = N <= 32), staged once
+template <int BM, bool SYM>
 __global__ void __launch_bounds__(256, 2) ts_gemm_tn_kernel(int M, int N, long K, double alpha,
                                                            const float* __restrict__ A, long lda,
                                                            const float* __restrict__ B, long ldb,
                                                            double* __restrict__ C, long ldc) {
+  static_assert(BM == 64 || (BM == 32), "row tile");
+  static_assert(!SYM || BM == 32, "Gram tile");
+  constexpr int RI = BM / 8;                         // rows of A per lane
+  constexpr int SWS = (BM == 64) ? 3 : 2;
+  constexpr int ROWS = SYM ? BM : BM + 32;           // staged rows per chunk
+  constexpr int STAGE = ROWS * TS_KC;                // floats per stage
+  constexpr int PIECES = ROWS * 8 / 256;             // 16-byte copies per thread per chunk
   extern __shared__ __align__(16) float ts_smem[];
-  constexpr int STAGE = (TS_BM + 32) * TS_KC;       // floats per stage: A rows then B rows
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const long i0 = (long)blockIdx.y * TS_BM;
+  const long i0 = (long)blockIdx.y * BM;
   const long kbeg = (long)blockIdx.x * TS_KS;
   const long kend = min(K, kbeg + TS_KS);
   const int nch = (int)((kend - kbeg + TS_KC - 1) / TS_KC);
-  // copies of one chunk: 96 rows x 8 groups = 768 16-byte pieces, three per thread
   auto issue = [&](int ch) {
     float* st = ts_smem + (ch % TS_STAGES) * STAGE;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < PIECES; ++q) {
       const int e = tid + 256 * q;
       const int row = e >> 3, g = e & 7;
       const long k = kbeg + (long)ch * TS_KC + 4 * g;
       const float* src;
       bool ok;
-      if (row < TS_BM) {
+      if (row < BM) {
         const long i = i0 + row;
         ok = (i < M) && (k < kend);
         src = ok ? A + i * lda + k : A;
       } else {
-        const int j = row - TS_BM;
+        const int j = row - BM;
         ok = (j < N) && (k < kend);
         src = ok ? B + (long)j * ldb + k : B;
       }
-      cp_async16(st + ts_off(row, g), src, ok);
+      cp_async16(st + ts_off<SWS>(row, g), src, ok);
     }
   };
 #pragma unroll
@@ -229,9 +236,9 @@ __global__ void __launch_bounds__(256, 2) ts_gemm_tn_kernel(int M, int N, long K
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
   const int ib = lane >> 2, jb = lane & 3;
-  float2 acc[8][4];
+  float2 acc[RI][4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < RI; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
   for (int ch = 0; ch < nch; ++ch) {
@@ -240,21 +247,21 @@ __global__ void __launch_bounds__(256, 2) ts_gemm_tn_kernel(int M, int N, long K
     if (ch + TS_STAGES - 1 < nch) issue(ch + TS_STAGES - 1);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     const float* as = ts_smem + (ch % TS_STAGES) * STAGE;
-    const float* bs = as + TS_BM * TS_KC;
+    const float* bs = SYM ? as : as + BM * TS_KC;
     // this warp's four k values: group `warp` of every row
     float2 bp[4][4];    // [k][j pair]
 #pragma unroll
     for (int jp = 0; jp < 4; ++jp) {
-      const float4 u = *reinterpret_cast<const float4*>(bs + ts_off(8 * jb + 2 * jp, warp));
-      const float4 v = *reinterpret_cast<const float4*>(bs + ts_off(8 * jb + 2 * jp + 1, warp));
+      const float4 u = *reinterpret_cast<const float4*>(bs + ts_off<SWS>(8 * jb + 2 * jp, warp));
+      const float4 v = *reinterpret_cast<const float4*>(bs + ts_off<SWS>(8 * jb + 2 * jp + 1, warp));
       bp[0][jp] = make_float2(u.x, v.x);
       bp[1][jp] = make_float2(u.y, v.y);
       bp[2][jp] = make_float2(u.z, v.z);
       bp[3][jp] = make_float2(u.w, v.w);
     }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float4 a = *reinterpret_cast<const float4*>(as + ts_off(8 * ib + i, warp));
+    for (int i = 0; i < RI; ++i) {
+      const float4 a = *reinterpret_cast<const float4*>(as + ts_off<SWS>(RI * ib + i, warp));
       const float ak[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
@@ -267,19 +274,19 @@ __global__ void __launch_bounds__(256, 2) ts_gemm_tn_kernel(int M, int N, long K
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
   // eight warp partials -> double sums -> atomics
-  float* red = ts_smem;                              // [8][64][32]
+  float* red = ts_smem;                              // [8][BM][32]
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < RI; ++i)
 #pragma unroll
     for (int jp = 0; jp < 4; ++jp)
-      *reinterpret_cast<float2*>(red + ((size_t)warp * 64 + 8 * ib + i) * 32 + 8 * jb + 2 * jp) = acc[i][jp];
+      *reinterpret_cast<float2*>(red + ((size_t)warp * BM + RI * ib + i) * 32 + 8 * jb + 2 * jp) = acc[i][jp];
   __syncthreads();
-  for (int o = tid; o < 64 * 32; o += 256) {
+  for (int o = tid; o < BM * 32; o += 256) {
     const int i = o >> 5, j = o & 31;
     if (i0 + i >= M || j >= N) continue;
     double sum = 0.0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) sum += (double)red[w * 64 * 32 + o];
+    for (int w = 0; w < 8; ++w) sum += (double)red[w * BM * 32 + o];
     atomicAdd(C + (i0 + i) * ldc + j, alpha * sum);
   }
 }
@@ -353,24 +360,34 @@ __global__ void __launch_bounds__(256) ts_gemm_nn_kernel(int M, long N, int K, d
 
 bool aligned(const void* p, size_t b) { return ((uintptr_t)p % b) == 0; }
 
+template <int BM, bool SYM>
+cudaError_t ts_tn_launch(int M, int N, long K, double alpha, const float* A, long lda, const float* B,
+                         long ldb, double* C, long ldc, cudaStream_t st) {
+  // the reduction area (8 x BM x 32 floats) and the staging ring, whichever is larger
+  constexpr size_t red = 8 * (size_t)BM * 32 * sizeof(float);
+  constexpr size_t ring = (size_t)TS_STAGES * (SYM ? BM : BM + 32) * TS_KC * sizeof(float);
+  constexpr size_t smem = red > ring ? red : ring;
+  static std::once_flag once;
+  static cudaError_t once_st = cudaSuccess;
+  cudaError_t e0 = once_status(once, once_st, [&] {
+    return cudaFuncSetAttribute(ts_gemm_tn_kernel<BM, SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e0 != cudaSuccess) return e0;
+  dim3 grid((unsigned)((K + TS_KS - 1) / TS_KS), (unsigned)((M + BM - 1) / BM));
+  ts_gemm_tn_kernel<BM, SYM><<<grid, 256, smem, st>>>(M, N, K, alpha, A, lda, B, ldb, C, ldc); note_launch();
+  return cudaGetLastError();
+}
+
 // C = alpha A B^T + beta C, A M x K, B N x K (both row-major), N <= 32
 cudaError_t ts_gemm_tn(int M, int N, long K, double alpha, const float* A, long lda, const float* B,
                        long ldb, double beta, double* C, long ldc, cudaStream_t st) {
   const long tot = (long)M * N;
   scale_matrix_kernel<double><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, C, ldc, beta); note_launch();
   if (K == 0) return cudaGetLastError();
-  // the reduction area (8 x 64 x 32 floats) covers the four staging buffers
-  constexpr size_t smem = 8 * 64 * 32 * sizeof(float);
-  static_assert(smem >= (size_t)TS_STAGES * (TS_BM + 32) * TS_KC * sizeof(float), "smem");
-  static std::once_flag once;
-  static cudaError_t once_st = cudaSuccess;
-  cudaError_t e0 = once_status(once, once_st, [&] {
-    return cudaFuncSetAttribute(ts_gemm_tn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  });
-  if (e0 != cudaSuccess) return e0;
-  dim3 grid((unsigned)((K + TS_KS - 1) / TS_KS), (unsigned)((M + TS_BM - 1) / TS_BM));
-  ts_gemm_tn_kernel<<<grid, 256, smem, st>>>(M, N, K, alpha, A, lda, B, ldb, C, ldc); note_launch();
-  return cudaGetLastError();
+  if (M <= 32 && A == B && lda == ldb && M == N)
+    return ts_tn_launch<32, true>(M, N, K, alpha, A, lda, B, ldb, C, ldc, st);
+  if (M <= 32) return ts_tn_launch<32, false>(M, N, K, alpha, A, lda, B, ldb, C, ldc, st);
+  return ts_tn_launch<64, false>(M, N, K, alpha, A, lda, B, ldb, C, ldc, st);
 }
 
 template <int MT>
