@@ -212,7 +212,9 @@ template cudaError_t fft3d<double>(double2*, long, int, int, const double2*, cud
 //   S [NS]          the full sphere (+G and -G), ordered by column, then z
 //   I1[N][NC]       z-transformed columns             (z, column)
 //   I2[N][N][NX]    y-transformed band                (z, y, x slot)
-// and each transformed line is exactly the zero-padded full-grid line's transform.
+// and each transformed line is exactly the zero-padded full-grid line's transform. Where a
+// z plane (two copies) fits in shared memory, the y and x passes run fused, one CTA per
+// plane, and I2 is never written.
 // ---------------------------------------------------------------------------------
 
 template <typename C, int N>
@@ -354,11 +356,152 @@ __global__ void __launch_bounds__(256) sph_x_kernel(cplx<T>* __restrict__ I2, cp
   }
 }
 
+// ---- fused y + x passes: one CTA per (grid, z plane) ----
+// Two-stage radix plans (N = R0 * R1), so a plane needs one out-of-place row stage in
+// shared memory. Composite radices 6, 9 and 12 run as two small DFTs in registers with
+// twiddles taken from the N-point table.
+template <int N> struct Plan2;
+template <> struct Plan2<16> { static constexpr int r0 = 4, r1 = 4; };
+template <> struct Plan2<32> { static constexpr int r0 = 8, r1 = 4; };
+template <> struct Plan2<48> { static constexpr int r0 = 8, r1 = 6; };
+template <> struct Plan2<64> { static constexpr int r0 = 8, r1 = 8; };
+template <> struct Plan2<72> { static constexpr int r0 = 8, r1 = 9; };
+template <> struct Plan2<96> { static constexpr int r0 = 8, r1 = 12; };
+
+// X[k1 + A k2] = sum_n v[n] w^(n k), w = exp(sign 2 pi i / (A B)), n = B n1 + n2; tw[m] is
+// exp(sign 2 pi i m / N) and A B divides N
+template <typename C, int A, int B, int N>
+__device__ __forceinline__ void dft_composite(C* v, int sign, const C* tw) {
+  constexpr int R = A * B;
+  C y[R];
+#pragma unroll
+  for (int n2 = 0; n2 < B; ++n2) {
+    C t[A];
+#pragma unroll
+    for (int n1 = 0; n1 < A; ++n1) t[n1] = v[B * n1 + n2];
+    Dft<C, A>::run(t, sign);
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) y[n2 * A + k1] = (n2 * k1 == 0) ? t[k1] : cmul(t[k1], tw[(n2 * k1 * (N / R)) % N]);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) {
+    C t[B];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) t[n2] = y[n2 * A + k1];
+    Dft<C, B>::run(t, sign);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = t[k2];
+  }
+}
+
+template <typename C, int R, int N>
+__device__ __forceinline__ void dft_any(C* v, int sign, const C* tw) {
+  if constexpr (R == 6) dft_composite<C, 2, 3, N>(v, sign, tw);
+  else if constexpr (R == 9) dft_composite<C, 3, 3, N>(v, sign, tw);
+  else if constexpr (R == 12) dft_composite<C, 4, 3, N>(v, sign, tw);
+  else Dft<C, R>::run(v, sign);
+}
+
+// line buffer addressing: element q of line l at l * LS + q + q / 16 (odd LS)
+template <int N>
+__device__ __forceinline__ int lidx(int l, int q) { return l * Pad<N>::LS + q + (q >> 4); }
+
+// One Stockham stage of radix R over n_lines lines of length N, Ns = product of the
+// earlier radices. Load / store go through functors ld(line, q) and st(line, q, value).
+template <typename C, int N, int R, typename LD, typename ST>
+__device__ __forceinline__ void pstage(int Ns, int sign, int n_lines, const C* tw, LD ld, ST st) {
+  constexpr int NB = N / R;
+  const int step = N / (Ns * R);
+  for (int e = threadIdx.x; e < n_lines * NB; e += blockDim.x) {
+    const int i = e / NB, j = e - i * NB;
+    const int k = j % Ns;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = ld(i, j + r * NB);
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[(r * k * step) % N]);
+    dft_any<C, R, N>(v, sign, tw);
+    const int o = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) st(i, o + r * Ns, v[r]);
+  }
+}
+
+template <typename T, int N>
+constexpr size_t plane_smem() {
+  // column buffer A [NX <= N/2 + 1 slots] + (column buffer B | row plane P) + twiddles + slots
+  constexpr int NXM = N / 2 + 1;
+  return (size_t)(NXM * Pad<N>::LS + N * Pad<N>::LS + N) * sizeof(cplx<T>) + (size_t)N * sizeof(int);
+}
+
+// inverse: I1[g][z][.] (z-transformed columns) -> grid plane (g, z); forward: the reverse.
+// Column buffers hold the band's x slots as lines over y; the row plane holds lines over x.
+template <typename T, int N, bool INV>
+__global__ void __launch_bounds__(256) sph_plane_kernel(cplx<T>* __restrict__ I1, cplx<T>* __restrict__ grid,
+                                                       SphereMap m, int sign, const cplx<T>* __restrict__ table) {
+  using C = cplx<T>;
+  constexpr int R0 = Plan2<N>::r0, R1 = Plan2<N>::r1;
+  constexpr int NXM = N / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* colA = reinterpret_cast<C*>(smem_raw);          // [NXM][LS]
+  C* colB = colA + NXM * Pad<N>::LS;                 // [NXM][LS], shares space with P
+  C* P = colB;                                       // [N][LS]
+  C* tw = P + N * Pad<N>::LS;
+  int* slot = reinterpret_cast<int*>(tw + N);        // slot of x in the band, -1 outside
+  load_twiddles<C, N>(tw, table, sign);
+  for (int x = threadIdx.x; x < N; x += blockDim.x) slot[x] = -1;
+  __syncthreads();
+  for (int l = threadIdx.x; l < m.NX; l += blockDim.x) slot[m.xs[l]] = l;
+  const long gz = blockIdx.x;                        // g * N + z
+  C* I1r = I1 + gz * m.NC;
+  C* Gp = grid + gz * (long)N * N;
+  const int nx = m.NX;
+  if (INV) {
+    for (int e = threadIdx.x; e < nx * Pad<N>::LS; e += blockDim.x) colA[e] = cmk<C>(0, 0);
+    __syncthreads();
+    for (int c = threadIdx.x; c < m.NC; c += blockDim.x) colA[lidx<N>(m.cxi[c], m.cy[c])] = I1r[c];
+    __syncthreads();
+    // y lines of the band: A -> B -> A
+    pstage<C, N, R0>(1, sign, nx, tw, [&](int l, int q) { return colA[lidx<N>(l, q)]; },
+                     [&](int l, int q, C v) { colB[lidx<N>(l, q)] = v; });
+    __syncthreads();
+    pstage<C, N, R1>(R0, sign, nx, tw, [&](int l, int q) { return colB[lidx<N>(l, q)]; },
+                     [&](int l, int q, C v) { colA[lidx<N>(l, q)] = v; });
+    __syncthreads();
+    // x lines: the first stage reads the band from the column buffer (zero outside it),
+    // the second writes the plane to global memory
+    pstage<C, N, R0>(1, sign, N, tw,
+                     [&](int y, int x) { const int s = slot[x]; return s >= 0 ? colA[lidx<N>(s, y)] : cmk<C>(0, 0); },
+                     [&](int y, int x, C v) { P[lidx<N>(y, x)] = v; });
+    __syncthreads();
+    pstage<C, N, R1>(R0, sign, N, tw, [&](int y, int x) { return P[lidx<N>(y, x)]; },
+                     [&](int y, int x, C v) { Gp[y * N + x] = v; });
+  } else {
+    // x lines: the first stage reads the plane from global memory, the second keeps the band
+    pstage<C, N, R0>(1, sign, N, tw, [&](int y, int x) { return Gp[y * N + x]; },
+                     [&](int y, int x, C v) { P[lidx<N>(y, x)] = v; });
+    __syncthreads();
+    pstage<C, N, R1>(R0, sign, N, tw, [&](int y, int x) { return P[lidx<N>(y, x)]; },
+                     [&](int y, int x, C v) { const int s = slot[x]; if (s >= 0) colA[lidx<N>(s, y)] = v; });
+    __syncthreads();
+    // y lines of the band: A -> B -> A
+    pstage<C, N, R0>(1, sign, nx, tw, [&](int l, int q) { return colA[lidx<N>(l, q)]; },
+                     [&](int l, int q, C v) { colB[lidx<N>(l, q)] = v; });
+    __syncthreads();
+    pstage<C, N, R1>(R0, sign, nx, tw, [&](int l, int q) { return colB[lidx<N>(l, q)]; },
+                     [&](int l, int q, C v) { colA[lidx<N>(l, q)] = v; });
+    __syncthreads();
+    for (int c = threadIdx.x; c < m.NC; c += blockDim.x) I1r[c] = colA[lidx<N>(m.cxi[c], m.cy[c])];
+  }
+}
+
 template <typename T, int N>
 static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>* I2, cplx<T>* grid,
                                  long n_grids, const SphereMap& m, const cplx<T>* table, cudaStream_t st) {
   constexpr int TL = Plan<N>::TX;
   const size_t smem = (size_t)(2 * TL * Pad<N>::LS + N) * sizeof(cplx<T>);
+  constexpr size_t psmem = plane_smem<T, N>();
+  constexpr bool use_plane = psmem <= 220 * 1024;
   static std::once_flag once;
   static cudaError_t once_st = cudaSuccess;
   cudaError_t e0 = once_status(once, once_st, [&] {
@@ -368,6 +511,12 @@ static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>*
                          (const void*)sph_x_kernel<T, N, true>, (const void*)sph_x_kernel<T, N, false>};
     for (const void* k : ks)
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if constexpr (use_plane) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sph_plane_kernel<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sph_plane_kernel<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    }
     return e;
   });
   if (e0 != cudaSuccess) return e0;
@@ -375,13 +524,22 @@ static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>*
   const long bz = n_grids * ((m.NC + TL - 1) / TL);
   const long by = n_grids * N * ((m.NX + TL - 1) / TL);
   const long bx = n_grids * N * (N / TL);
+  const long bp = n_grids * N;
   if (inverse) {
     sph_z_kernel<T, N, true><<<(unsigned)bz, 256, smem, st>>>(S, I1, m, +1, table); note_launch();
-    sph_y_kernel<T, N, true><<<(unsigned)by, 256, smem, st>>>(I1, I2, m, +1, table); note_launch();
-    sph_x_kernel<T, N, true><<<(unsigned)bx, 256, smem, st>>>(I2, grid, m, +1, table); note_launch();
+    if constexpr (use_plane) {
+      sph_plane_kernel<T, N, true><<<(unsigned)bp, 256, psmem, st>>>(I1, grid, m, +1, table); note_launch();
+    } else {
+      sph_y_kernel<T, N, true><<<(unsigned)by, 256, smem, st>>>(I1, I2, m, +1, table); note_launch();
+      sph_x_kernel<T, N, true><<<(unsigned)bx, 256, smem, st>>>(I2, grid, m, +1, table); note_launch();
+    }
   } else {
-    sph_x_kernel<T, N, false><<<(unsigned)bx, 256, smem, st>>>(I2, grid, m, -1, table); note_launch();
-    sph_y_kernel<T, N, false><<<(unsigned)by, 256, smem, st>>>(I1, I2, m, -1, table); note_launch();
+    if constexpr (use_plane) {
+      sph_plane_kernel<T, N, false><<<(unsigned)bp, 256, psmem, st>>>(I1, grid, m, -1, table); note_launch();
+    } else {
+      sph_x_kernel<T, N, false><<<(unsigned)bx, 256, smem, st>>>(I2, grid, m, -1, table); note_launch();
+      sph_y_kernel<T, N, false><<<(unsigned)by, 256, smem, st>>>(I1, I2, m, -1, table); note_launch();
+    }
     sph_z_kernel<T, N, false><<<(unsigned)bz, 256, smem, st>>>(S, I1, m, -1, table); note_launch();
   }
   return cudaGetLastError();

@@ -103,7 +103,7 @@ def test_apply_empty_block_is_noop(tiny):
 # ---------------------------------------------------------------------------------
 # localised orbitals on larger grids: odd N_occ, ragged sphere, pair-count rule
 # ---------------------------------------------------------------------------------
-@pytest.mark.parametrize("N,n_occ,seed", [(32, 12, 3), (48, 13, 4)])
+@pytest.mark.parametrize("N,n_occ,seed", [(32, 12, 3), (48, 13, 4), (64, 9, 9), (72, 8, 7), (96, 6, 8)])
 @pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
 def test_localized_operator_vs_matrix_free(N, n_occ, seed, prec, tol):
     inst = make_localized(seed, 20.0 * N / 72, N, n_occ, 2.5, 2 * n_occ, n_eig=4, block=4)
