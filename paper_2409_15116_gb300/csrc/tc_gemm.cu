@@ -26,7 +26,9 @@ namespace bse {
 constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 3;
 constexpr int TC_TILE = TC_BM * TC_BK * 2;          // 16 KB per operand tile (BM == BN)
 constexpr int TC_STAGE_BYTES = 4 * TC_TILE;         // A_hi, A_lo, B_hi, B_lo
-constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
+constexpr int TC_EPI_LD = 17;                        // floats per row of a warp's epilogue chunk
+constexpr int TC_EPI_BYTES = 4 * 32 * TC_EPI_LD * 4; // four warps x 32 rows x 16 (+1) floats
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256 + TC_EPI_BYTES;
 constexpr long long TC_WAIT_LIMIT = 1ll << 26;      // try_wait polls before giving up
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_bf16x3_kernel(
   uint64_t* empty = full + TC_STAGES;
   uint64_t* accb = empty + TC_STAGES;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(accb + 1);
+  float* epi = reinterpret_cast<float*>(base + TC_STAGES * TC_STAGE_BYTES + 256);   // [4][32][17]
   __shared__ int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
@@ -156,8 +159,11 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_bf16x3_kernel(
     const bool ok = __all_sync(0xffffffffu, mbar_wait(su32(accb), 0) ? 1 : 0) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) s_abort = 1;
-    const int row = m0 + warp * 32 + lane;
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    float* ew = epi + warp * 32 * TC_EPI_LD;
+    // lane (r4, q): rows r4 + 8 i of this warp's 32, columns 4 q .. 4 q + 3 of the chunk
+    const int q = lane & 3, r4 = lane >> 2;
+    const bool vec = (g.ldo % 4) == 0 && (((uintptr_t)g.out) % 16) == 0;
     if (ok) {
 #pragma unroll 1
       for (int c0 = 0; c0 < TC_BN; c0 += 16) {
@@ -169,16 +175,42 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_bf16x3_kernel(
               "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(taddr + c0));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row < g.M) {
-          float* o = g.out + (long)row * g.ldo + n0 + c0;
+        // transpose through shared memory: the accumulator comes one row per lane, the
+        // global accesses go as 16-byte pieces of eight rows per instruction
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            if (n0 + c0 + j >= g.N) break;
-            const float val = g.alpha * __uint_as_float(v[j]);
-            if (g.atomic) atomicAdd(o + j, val);
-            else o[j] = (g.beta == 0.f) ? val : val + g.beta * o[j];
+        for (int j = 0; j < 16; ++j) ew[lane * TC_EPI_LD + j] = g.alpha * __uint_as_float(v[j]);
+        __syncwarp();
+        const int col = n0 + c0 + 4 * q;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int rl = r4 + 8 * i;
+          const int row = m0 + warp * 32 + rl;
+          if (row >= g.M) continue;
+          const float* e = ew + rl * TC_EPI_LD + 4 * q;
+          float4 val = make_float4(e[0], e[1], e[2], e[3]);
+          float* o = g.out + (long)row * g.ldo + col;
+          if (vec && col + 3 < g.N) {
+            float4* o4 = reinterpret_cast<float4*>(o);
+            if (g.atomic) {
+              atomicAdd(o4, val);
+            } else {
+              if (g.beta != 0.f) {
+                const float4 old = *o4;
+                val.x += g.beta * old.x; val.y += g.beta * old.y; val.z += g.beta * old.z; val.w += g.beta * old.w;
+              }
+              *o4 = val;
+            }
+          } else {
+            const float vv[4] = {val.x, val.y, val.z, val.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              if (col + j >= g.N) break;
+              if (g.atomic) atomicAdd(o + j, vv[j]);
+              else o[j] = (g.beta == 0.f) ? vv[j] : vv[j] + g.beta * o[j];
+            }
           }
         }
+        __syncwarp();
       }
     }
   }
