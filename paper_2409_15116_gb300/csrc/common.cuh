@@ -42,8 +42,9 @@ __device__ __forceinline__ size_t pair_off(long f, long r, long n3) {
 
 // tau_p(r) for n_pairs pairs is stored point-tiled: tiles of TAU_TB consecutive grid
 // points, each holding all pairs' values at those points, [n3/TAU_TB][n_pairs][TAU_TB].
-// A CTA that works on a few points reads one contiguous stretch of tau.
-constexpr int TAU_TB = 16;
+// A CTA that works on a few points reads one contiguous stretch of tau, and a warp that
+// covers 32 points reads whole 128-byte lines.
+constexpr int TAU_TB = 32;
 __host__ __device__ __forceinline__ size_t tau_off(long p, long r, long n_pairs) {
   return ((size_t)(r / TAU_TB) * (size_t)n_pairs + (size_t)p) * TAU_TB + (size_t)(r % TAU_TB);
 }

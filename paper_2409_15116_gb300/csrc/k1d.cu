@@ -11,7 +11,7 @@
 //  * a(r) for every orbital of the chunk is copied into shared memory with cp.async
 //    (no registers held, all copies in flight at once), laid out [w][t][s] so that a lane
 //    reads the SC values it needs for orbital w as one or two 16-byte loads;
-//  * groups of TR lanes (one lane per point) walk row blocks of four orbitals (one
+//  * groups of TR lanes (one lane per point; TR = 8, 16 or 32) walk row blocks of four orbitals (one
 //    localisation site); each block lists the union of its rows' neighbours w, with the
 //    four pair indices (-1 where a row has no such neighbour, Eq. overlap);
 //  * tau values go straight from global memory to registers through a ring of PD entries,
@@ -242,8 +242,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k1d_tile_kernel(
 
 // tile variants: (points per CTA, vectors per CTA, threads per CTA)
 struct Variant { int tr, sc, nt; };
-constexpr Variant kVariants[] = {{0, 0, 0}, {16, 8, 512}, {8, 8, 256}, {16, 4, 256}, {8, 4, 256},
-                                 {16, 2, 256}, {16, 1, 256}, {16, 8, 256}, {8, 8, 512}};
+constexpr Variant kVariants[] = {{0, 0, 0},     {16, 8, 512}, {8, 8, 256},  {16, 4, 256},
+                                 {8, 4, 256},   {16, 2, 256}, {16, 1, 256}, {16, 8, 256},
+                                 {8, 8, 512},   {32, 4, 512}, {32, 8, 512}, {32, 2, 256}};
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0])) - 1;
 
 template <typename T>
@@ -322,6 +323,9 @@ cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, l
     BSE_K1D_CASE(6, 16, 1, 256)
     BSE_K1D_CASE(7, 16, 8, 256)
     BSE_K1D_CASE(8, 8, 8, 512)
+    BSE_K1D_CASE(9, 32, 4, 512)
+    BSE_K1D_CASE(10, 32, 8, 512)
+    BSE_K1D_CASE(11, 32, 2, 256)
     default: return cudaErrorInvalidValue;
   }
 #undef BSE_K1D_CASE

@@ -146,7 +146,7 @@ def ragged_case():
     return inst, A, Lop.apply(A)
 
 
-@pytest.mark.parametrize("variant", range(1, 9))
+@pytest.mark.parametrize("variant", range(1, 12))
 @pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
 def test_k1d_tile_variants_vs_matrix_free(ragged_case, variant, prec, tol, monkeypatch):
     inst, A, ref = ragged_case
