@@ -465,7 +465,7 @@ int build_tau_impl(bse_ctx* c) {
     CA(dalloc(c, &gram, (size_t)n * n));
     CA(dalloc(c, &dg, (size_t)n));
     CK(square_fields(n, c->upsi64, n3, rho, c->st));
-    CK((gemm<double, double>(false, true, n, n, (int)n3, 1.0, rho, n3, rho, n3, 0.0, gram, n, 0, c->st)));
+    CK((gram_sym<double, double>(n, (int)n3, 1.0, rho, n3, gram, n, c->st)));
     CK(normalize_overlap(n, gram, dg, c->st));
     c->O_h.assign((size_t)n * n, 0.0);
     CK(cudaMemcpyAsync(c->O_h.data(), gram, sizeof(double) * n * n, cudaMemcpyDeviceToHost, c->st));
@@ -626,7 +626,7 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
   CA(al(&Tt, (size_t)b * dim)); CA(al(&Tt2, (size_t)b * dim));
   CA(al(&S1, (size_t)keep * dim)); CA(al(&S2, (size_t)keep * dim));
   CA(al(&Yt, (size_t)ms * ms)); CA(al(&Cmt, (size_t)ms * b)); CA(al(&Lt, (size_t)b * b));
-  CA(al(&Hs, (size_t)ms * ms)); CA(al(&Yv, (size_t)ms * ms)); CA(al(&jw, (size_t)4 * ms * ms));
+  CA(al(&Hs, (size_t)ms * ms)); CA(al(&Yv, (size_t)ms * ms)); CA(al(&jw, (size_t)4 * ms * ms + 2 * (size_t)ms));
   CA(al(&theta, (size_t)ms)); CA(al(&nrm, (size_t)ms)); CA(al(&Cm, (size_t)ms * b));
   CA(al(&Sg, (size_t)b * b)); CA(al(&Linv, (size_t)b * b));
   CA(al(&info, 4)); CA(al(&which, (size_t)b));

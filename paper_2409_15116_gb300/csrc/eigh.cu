@@ -50,10 +50,15 @@ __device__ int sturm_count(int m, const R* d, const R* e2, R x, R pivmin) {
   return cnt;
 }
 
+// Z (eigenvectors of T, vector j at Z + j * zld) and S (elimination factors, 3 m per
+// vector at S + j * sld) live in shared memory after the matrix when they fit, else in the
+// global work buffer; the odd strides keep one-thread-per-vector loops free of bank
+// conflicts.
 template <typename R>
 __global__ void __launch_bounds__(512) eigh_lowest_kernel(int m, int k, const double* __restrict__ Ain,
-                                                         long lda, R* __restrict__ Z,
-                                                         R* __restrict__ S, double* __restrict__ V,
+                                                         long lda, R* __restrict__ Zg,
+                                                         R* __restrict__ Sg, int in_smem,
+                                                         double* __restrict__ V,
                                                          double* __restrict__ w, int* info) {
   using Tol = EighTol<R>;
   extern __shared__ __align__(16) unsigned char eigh_smem[];
@@ -64,7 +69,11 @@ __global__ void __launch_bounds__(512) eigh_lowest_kernel(int m, int k, const do
   R* e2 = e + m;                // m
   R* p = e2 + m;                // m
   R* lam = p + m;               // EIGH_KMAX
+  const int zld = m | 1, sld = (3 * m) | 1;
+  R* Z = in_smem ? lam + EIGH_KMAX : Zg;
+  R* S = in_smem ? Z + (long)k * zld : Sg;
   __shared__ R red[32];
+  __shared__ R dots[EIGH_KMAX];
   __shared__ R s_alpha, s_scale;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (long x = tid; x < (long)m * m; x += nt) {
@@ -83,11 +92,11 @@ __global__ void __launch_bounds__(512) eigh_lowest_kernel(int m, int k, const do
       const R nrm = sqrt(s2);
       const R alpha = (x0 >= 0) ? -nrm : nrm;
       d[c] = A[c * ld + c];
-      e[c] = (nrm == 0.0) ? 0.0 : alpha;
+      e[c] = (nrm == (R)0) ? (R)0 : alpha;
       // v = x - alpha e1, |v|^2 = s2 - 2 alpha x0 + alpha^2
-      const R vn2 = s2 - 2.0 * alpha * x0 + alpha * alpha;
+      const R vn2 = s2 - (R)2 * alpha * x0 + alpha * alpha;
       s_alpha = alpha;
-      s_scale = (nrm == 0.0 || vn2 <= 0.0) ? 0.0 : 1.0 / sqrt(vn2);
+      s_scale = (nrm == (R)0 || vn2 <= (R)0) ? (R)0 : (R)1 / sqrt(vn2);
     }
     __syncthreads();
     const R sc = s_scale;
@@ -97,13 +106,18 @@ __global__ void __launch_bounds__(512) eigh_lowest_kernel(int m, int k, const do
       A[(c + 1 + i) * ld + c] = (i == 0 ? x - s_alpha : x) * sc;
     }
     __syncthreads();
-    if (sc == 0.0) continue;
-    // p = B u over the trailing block B = A[c+1:, c+1:] (symmetric, both halves valid)
-    for (int i = tid; i < n; i += nt) {
-      R acc = 0;
-      const R* row = A + (c + 1 + i) * ld + (c + 1);
-      for (int j = 0; j < n; ++j) acc += row[j] * A[(c + 1 + j) * ld + c];
-      p[i] = acc;
+    if (sc == (R)0) continue;
+    // p = B u over the trailing block B = A[c+1:, c+1:] (symmetric, both halves valid):
+    // one warp per row, lanes along the row, shuffle reduction
+    {
+      const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+      for (int i = wid; i < n; i += nw) {
+        const R* row = A + (c + 1 + i) * ld + (c + 1);
+        R acc = 0;
+        for (int j = lane; j < n; j += 32) acc += row[j] * A[(c + 1 + j) * ld + c];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) p[i] = acc;
+      }
     }
     R kk = 0;
     __syncthreads();
@@ -112,10 +126,14 @@ __global__ void __launch_bounds__(512) eigh_lowest_kernel(int m, int k, const do
     // q = p - K u (kept in p), B -= 2 (u q^T + q u^T)
     for (int i = tid; i < n; i += nt) p[i] -= kk * A[(c + 1 + i) * ld + c];
     __syncthreads();
-    for (int x = tid; x < n * n; x += nt) {
-      const int i = x / n, j = x - i * n;
-      const R ui = A[(c + 1 + i) * ld + c], uj = A[(c + 1 + j) * ld + c];
-      A[(c + 1 + i) * ld + (c + 1 + j)] -= 2.0 * (ui * p[j] + p[i] * uj);
+    {
+      // rank-2 update, one warp per row (no per-element index division)
+      const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+      for (int i = wid; i < n; i += nw) {
+        const R ui = A[(c + 1 + i) * ld + c], pi = p[i];
+        R* row = A + (c + 1 + i) * ld + (c + 1);
+        for (int j = lane; j < n; j += 32) row[j] -= (R)2 * (ui * p[j] + pi * A[(c + 1 + j) * ld + c]);
+      }
     }
     __syncthreads();
   }
@@ -125,7 +143,7 @@ __global__ void __launch_bounds__(512) eigh_lowest_kernel(int m, int k, const do
       e[m - 2] = A[(m - 1) * ld + (m - 2)];
     }
     d[m - 1] = A[(m - 1) * ld + (m - 1)];
-    e[m - 1] = 0.0;
+    e[m - 1] = (R)0;
   }
   __syncthreads();
   for (int i = tid; i < m; i += nt) e2[i] = e[i] * e[i];
@@ -133,26 +151,36 @@ __global__ void __launch_bounds__(512) eigh_lowest_kernel(int m, int k, const do
   // ---- 2. bisection for the k lowest eigenvalues ----
   R gl = (R)1e30, gu = (R)-1e30, tnorm = 0;
   for (int i = 0; i < m; ++i) {
-    const R r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
+    const R r = (i > 0 ? fabs(e[i - 1]) : (R)0) + (i + 1 < m ? fabs(e[i]) : (R)0);
     gl = fmin(gl, d[i] - r);
     gu = fmax(gu, d[i] + r);
   }
   tnorm = fmax(fabs(gl), fabs(gu));
   const R pivmin = Tol::pivtiny + Tol::tiny * tnorm * tnorm;
-  for (int j = tid; j < k; j += nt) {
-    R lo = gl - 50 * Tol::eps * tnorm - Tol::tiny, hi = gu + 50 * Tol::eps * tnorm + Tol::tiny;
-    for (int it = 0; it < 200 && hi - lo > Tol::eps * fmax(fabs(lo), fabs(hi)) + Tol::tiny; ++it) {
-      const R mid = 0.5 * (lo + hi);
-      if (mid <= lo || mid >= hi) break;
-      if (sturm_count(m, d, e2, mid, pivmin) > j) hi = mid; else lo = mid;
+  // multisection: warp w brackets eigenvalues j = w, w + nw, ...; its 32 lanes evaluate the
+  // Sturm count at 32 interior points of the current bracket, which shrinks 33-fold a step
+  {
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    for (int j = wid; j < k; j += nw) {
+      R lo = gl - 50 * Tol::eps * tnorm - Tol::tiny, hi = gu + 50 * Tol::eps * tnorm + Tol::tiny;
+      for (int it = 0; it < 64; ++it) {
+        if (!(hi - lo > Tol::eps * fmax(fabs(lo), fabs(hi)) + Tol::tiny)) break;
+        const R x = lo + (hi - lo) * (R)(lane + 1) / (R)33;
+        const int cnt = sturm_count(m, d, e2, x, pivmin);
+        const int q = __popc(__ballot_sync(0xffffffffu, cnt <= j));
+        const R nlo = (q == 0) ? lo : lo + (hi - lo) * (R)q / (R)33;
+        const R nhi = (q == 32) ? hi : lo + (hi - lo) * (R)(q + 1) / (R)33;
+        if (!(nlo > lo || nhi < hi)) break;        // no progress at this precision
+        lo = nlo; hi = nhi;
+      }
+      if (lane == 0) lam[j] = (R)0.5 * (lo + hi);
     }
-    lam[j] = 0.5 * (lo + hi);
   }
   __syncthreads();
   // ---- 3. inverse iteration, one thread per eigenvector (Z column-major, m x k) ----
   const R ortol = (R)1e-3 * tnorm;
   for (int j = tid; j < k; j += nt) {
-    R* z = Z + (long)j * m;
+    R* z = Z + (long)j * zld;
     // perturb the shift slightly inside clusters so the factorisation stays regular
     R mu = lam[j];
     for (int i = 0; i < j; ++i)
@@ -161,14 +189,14 @@ __global__ void __launch_bounds__(512) eigh_lowest_kernel(int m, int k, const do
     for (int pass = 0; pass < 3; ++pass) {
       // solve (T - mu I) y = z by elimination with partial pivoting; the upper factor has
       // up to two super-diagonals (u0 diag, u1, u2); y overwrites z
-      R* u0 = S + (long)j * 3 * m;
+      R* u0 = S + (long)j * sld;
       R* u1 = u0 + m;
       R* u2 = u1 + m;
-      R a0 = d[0] - mu, b0 = (m > 1) ? e[0] : 0.0, c0 = 0.0;
+      R a0 = d[0] - mu, b0 = (m > 1) ? e[0] : (R)0, c0 = (R)0;
       R rhs = z[0];
       for (int i = 0; i + 1 < m; ++i) {
         const R sub = e[i];
-        const R a1 = d[i + 1] - mu, b1 = (i + 2 < m) ? e[i + 1] : 0.0;
+        const R a1 = d[i + 1] - mu, b1 = (i + 2 < m) ? e[i + 1] : (R)0;
         R r1 = z[i + 1];
         if (fabs(sub) > fabs(a0)) {          // swap rows i and i+1
           const R f = a0 / sub;
@@ -176,16 +204,16 @@ __global__ void __launch_bounds__(512) eigh_lowest_kernel(int m, int k, const do
           z[i] = r1;
           const R na0 = b0 - f * a1, nb0 = c0 - f * b1;
           r1 = rhs - f * r1;
-          a0 = na0; b0 = nb0; c0 = 0.0; rhs = r1;
+          a0 = na0; b0 = nb0; c0 = (R)0; rhs = r1;
         } else {
-          if (a0 == 0.0) a0 = pivmin;
+          if (a0 == (R)0) a0 = pivmin;
           const R f = sub / a0;
           u0[i] = a0; u1[i] = b0; u2[i] = c0;
           z[i] = rhs;
-          a0 = a1 - f * b0; b0 = b1 - f * c0; c0 = 0.0; rhs = r1 - f * rhs;
+          a0 = a1 - f * b0; b0 = b1 - f * c0; c0 = (R)0; rhs = r1 - f * rhs;
         }
       }
-      if (a0 == 0.0) a0 = pivmin;
+      if (a0 == (R)0) a0 = pivmin;
       u0[m - 1] = a0;
       z[m - 1] = rhs;
       // back substitution
@@ -202,22 +230,38 @@ __global__ void __launch_bounds__(512) eigh_lowest_kernel(int m, int k, const do
     }
   }
   __syncthreads();
-  // re-orthogonalise inside clusters (modified Gram-Schmidt in eigenvalue order)
-  for (int j = 1; j < k; ++j) {
-    for (int i = 0; i < j; ++i) {
-      if (fabs(lam[j] - lam[i]) > ortol) continue;
-      R dot = 0;
-      for (int r = tid; r < m; r += nt) dot += Z[(long)i * m + r] * Z[(long)j * m + r];
-      dot = blk_sum(dot, red);
-      for (int r = tid; r < m; r += nt) Z[(long)j * m + r] -= dot * Z[(long)i * m + r];
+  // re-orthogonalise inside clusters (eigenvalues within ortol), in eigenvalue order: the
+  // projections on all earlier members at once (one warp per member), twice
+  {
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    for (int j = 1; j < k; ++j) {
+      bool any = false;
+      for (int i = 0; i < j; ++i) any |= fabs(lam[j] - lam[i]) <= ortol;
+      if (any) {
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int i = wid; i < j; i += nw) {
+            R dt = 0;
+            if (fabs(lam[j] - lam[i]) <= ortol)
+              for (int r = lane; r < m; r += 32) dt += Z[(long)i * zld + r] * Z[(long)j * zld + r];
+            for (int o = 16; o > 0; o >>= 1) dt += __shfl_xor_sync(0xffffffffu, dt, o);
+            if (lane == 0) dots[i] = dt;
+          }
+          __syncthreads();
+          for (int r = tid; r < m; r += nt) {
+            R acc = 0;
+            for (int i = 0; i < j; ++i) acc += dots[i] * Z[(long)i * zld + r];
+            Z[(long)j * zld + r] -= acc;
+          }
+          __syncthreads();
+        }
+      }
+      R nn = 0;
+      for (int r = tid; r < m; r += nt) nn += Z[(long)j * zld + r] * Z[(long)j * zld + r];
+      nn = blk_sum(nn, red);
+      const R inv = (R)1 / sqrt(nn);
+      for (int r = tid; r < m; r += nt) Z[(long)j * zld + r] *= inv;
       __syncthreads();
     }
-    R nn = 0;
-    for (int r = tid; r < m; r += nt) nn += Z[(long)j * m + r] * Z[(long)j * m + r];
-    nn = blk_sum(nn, red);
-    const R inv = (R)1 / sqrt(nn);
-    for (int r = tid; r < m; r += nt) Z[(long)j * m + r] *= inv;
-    __syncthreads();
   }
   // ---- 4. back-transformation: v = H_0 H_1 ... H_{m-3} z, applied to all k vectors ----
   for (int c = m - 3; c >= 0; --c) {
@@ -225,40 +269,43 @@ __global__ void __launch_bounds__(512) eigh_lowest_kernel(int m, int k, const do
     // one warp per vector: dot = u . z[c+1:], z[c+1:] -= 2 dot u
     const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     for (int j = wid; j < k; j += nw) {
-      R* z = Z + (long)j * m;
+      R* z = Z + (long)j * zld;
       R dot = 0;
       for (int i = lane; i < n; i += 32) dot += A[(c + 1 + i) * ld + c] * z[c + 1 + i];
       for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-      for (int i = lane; i < n; i += 32) z[c + 1 + i] -= 2.0 * dot * A[(c + 1 + i) * ld + c];
+      for (int i = lane; i < n; i += 32) z[c + 1 + i] -= (R)2 * dot * A[(c + 1 + i) * ld + c];
     }
     __syncthreads();
   }
   // outputs: V row-major m x k (component r of eigenvector j at V[r*k + j]), w[0..k)
   for (long x = tid; x < (long)m * k; x += nt) {
     const int r = (int)(x / k), j = (int)(x - (long)r * k);
-    V[x] = (double)Z[(long)j * m + r];
+    V[x] = (double)Z[(long)j * zld + r];
   }
   for (int j = tid; j < k; j += nt) w[j] = (double)lam[j];
   if (tid == 0) info[0] = 0;
 }
 
 // k lowest eigenpairs of the symmetric m x m matrix A (lda): eigenvalues ascending in w[0..k),
-// eigenvectors as the columns of V (row-major m x k). work: at least 4*m*k doubles.
+// eigenvectors as the columns of V (row-major m x k). work: at least 4*m*k + 2*k doubles.
 // single: single-precision arithmetic (double input and outputs).
 template <typename R>
 static cudaError_t launch_eigh(int m, int k, const double* A, long lda, double* work, double* V, double* w,
                                int* info, cudaStream_t st) {
-  const size_t smem = ((size_t)m * (m + 1) + 4 * (size_t)m + EIGH_KMAX) * sizeof(R);
+  constexpr size_t SMEM_MAX = 220 * 1024;
+  const size_t base = ((size_t)m * (m + 1) + 4 * (size_t)m + EIGH_KMAX) * sizeof(R);
+  const size_t extra = ((size_t)k * (m | 1) + (size_t)k * ((3 * m) | 1)) * sizeof(R);
+  const bool in_smem = base + extra <= SMEM_MAX;
+  const size_t smem = in_smem ? base + extra : base;
   static std::once_flag once;
   static cudaError_t once_st = cudaSuccess;
   cudaError_t e0 = once_status(once, once_st, [&] {
-    const size_t mx = ((size_t)EIGH_MAX * (EIGH_MAX + 1) + 4 * EIGH_MAX + EIGH_KMAX) * sizeof(R);
-    return cudaFuncSetAttribute(eigh_lowest_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    return cudaFuncSetAttribute(eigh_lowest_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
   });
   if (e0 != cudaSuccess) return e0;
-  R* Z = reinterpret_cast<R*>(work);       // m x k, column-major
-  R* scratch = Z + (size_t)m * k;          // 3 m per vector
-  eigh_lowest_kernel<R><<<1, 512, smem, st>>>(m, k, A, lda, Z, scratch, V, w, info);
+  R* Z = reinterpret_cast<R*>(work);       // k vectors of stride m | 1
+  R* scratch = Z + (size_t)k * (m | 1);    // k x ((3 m) | 1)
+  eigh_lowest_kernel<R><<<1, 512, smem, st>>>(m, k, A, lda, Z, scratch, in_smem ? 1 : 0, V, w, info);
   note_launch();
   return cudaGetLastError();
 }

@@ -11,7 +11,7 @@
 
 namespace bse {
 
-template <typename T, typename TC, bool AT, bool BT, int TM, int TN, bool DFLUSH>
+template <typename T, typename TC, bool AT, bool BT, int TM, int TN, bool DFLUSH, bool TRI = false>
 __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, double alpha,
                                                   const T* __restrict__ A, long lda,
                                                   const T* __restrict__ B, long ldb, double beta,
@@ -21,7 +21,16 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, double a
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const long i0 = (long)blockIdx.y * BM, j0 = (long)blockIdx.x * BN;
+  long ti = blockIdx.y, tj = blockIdx.x;
+  if constexpr (TRI) {
+    // blockIdx.x enumerates the tiles (ti <= tj) of the upper triangle, row by row
+    const int nt = (N + BN - 1) / BN;
+    long r = blockIdx.x;
+    ti = 0;
+    while (r >= nt - ti) { r -= nt - ti; ++ti; }
+    tj = ti + r;
+  }
+  const long i0 = ti * BM, j0 = tj * BN;
   const long kbeg = (long)blockIdx.z * k_chunk;
   const long kend = (kbeg + k_chunk < K) ? kbeg + k_chunk : K;
   T acc[TM][TN];
@@ -410,6 +419,47 @@ cudaError_t ts_gemm_nn(bool at, int M, long N, int K, double alpha, const float*
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------------
+// Symmetric Gram C = alpha A A^T (A n x K row-major, C n x n): only the tiles on and
+// above the diagonal are computed (split over K with atomics), then mirrored.
+// ---------------------------------------------------------------------------------
+namespace {
+template <typename TC>
+__global__ void mirror_upper_kernel(int n, TC* C, long ldc) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx - (long)i * n);
+  if (i > j) C[i * ldc + j] = C[(long)j * ldc + i];
+}
+}  // namespace
+
+template <typename T, typename TC>
+cudaError_t gram_sym(int n, int K, double alpha, const T* A, long lda, TC* C, long ldc, cudaStream_t st) {
+  constexpr int TM = 4, BM = 64;
+  if (n <= 0) return cudaSuccess;
+  constexpr bool DF = sizeof(T) < sizeof(TC);
+  const long nt = (n + BM - 1) / BM;
+  const long tiles = nt * (nt + 1) / 2;
+  long s = tiles >= 304 ? 1 : (304 + tiles - 1) / tiles;
+  const long kmax = (K + 255) / 256;
+  if (s > kmax) s = kmax;
+  if (s < 1) s = 1;
+  int k_chunk = (int)((K + s - 1) / s);
+  k_chunk = (k_chunk + 15) / 16 * 16;
+  if (k_chunk <= 0) k_chunk = 16;
+  const int splitk = (int)((K + k_chunk - 1) / k_chunk);
+  const long tot = (long)n * n;
+  scale_matrix_kernel<TC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, n, C, ldc, 0.0); note_launch();
+  if (K > 0) {
+    dim3 grid((unsigned)tiles, 1, (unsigned)(splitk < 1 ? 1 : splitk));
+    gemm_kernel<T, TC, false, true, TM, TM, DF, true><<<grid, 256, 0, st>>>(n, n, K, alpha, A, lda, A, lda, 0.0, C,
+                                                                           ldc, k_chunk, 1); note_launch();
+  }
+  mirror_upper_kernel<TC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, C, ldc); note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t gram_sym<double, double>(int, int, double, const double*, long, double*, long, cudaStream_t);
 
 // Tile shape follows the operands: a side of at most 16 gets a 16-wide tile, so the
 // tall-skinny products of the Davidson algebra (16-32 rows against millions of

@@ -51,6 +51,9 @@ cudaError_t grid_to_sphere(cplx<T>* grids, long n_fields, int n_pw, int n_half, 
                            const T* g2h, const T* esh, int n_occ, cudaStream_t st);
 
 // ---- gemm.cu ----
+// C = alpha A A^T, A n x K row-major: upper-triangle tiles, then mirrored
+template <typename T, typename TC>
+cudaError_t gram_sym(int n, int K, double alpha, const T* A, long lda, TC* C, long ldc, cudaStream_t st);
 template <typename T, typename TC>
 cudaError_t gemm(bool at, bool bt, int M, int N, int K, double alpha, const T* A, long lda,
                  const T* B, long ldb, double beta, TC* C, long ldc, int splitk, cudaStream_t st);
