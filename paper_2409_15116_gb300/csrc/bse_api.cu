@@ -597,6 +597,16 @@ template <typename T>
 using SampleHook = std::function<int(int, const T*, const T*, const std::vector<double>&,
                                      const std::vector<int>&)>;
 
+// C (M x N, double) = A B^T over the long dimension K: the Gram, Rayleigh-Ritz and CGS
+// coefficient products of the Davidson algebra (the tall-skinny SIMT kernel for N <= 32).
+// Tensor cores do not pay here: an MMA with N = 32 runs at an eighth of the pipe's rate,
+// and the three-term split that FP32 accuracy needs leaves them below the FP32 SIMT rate.
+template <typename T>
+cudaError_t tn_product(bse_ctx* c, int M, int N, long K, const T* A, long lda, const T* B, long ldb, double* C,
+                       long ldc) {
+  return gemm<T, double>(false, true, M, N, (int)K, 1.0, A, lda, B, ldb, 0.0, C, ldc, 0, c->st);
+}
+
 template <typename T>
 int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* vec_out,
                   bse_davidson_stats* stats, const SampleHook<T>* hook = nullptr) {
@@ -695,7 +705,7 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
     CK(set_unit<T>(x, dim, top.first.flat, c->st));
     CA(project<T>(c, c->n_occ, x, pcbuf));
     for (int pass = 0; pass < 2 && m > 0; ++pass) {
-      CK((gemm<T, double>(false, true, m, 1, (int)dim, 1.0, V, dim, x, dim, 0.0, Cm, 1, 0, c->st)));
+      CK(tn_product<T>(c, m, 1, dim, V, dim, x, dim, Cm, 1));
       CK((convert<double, T>(m, Cm, Cmt, c->st)));
       CK((gemm<T, T>(true, false, 1, (int)dim, m, -1.0, Cmt, 1, V, dim, 1.0, x, dim, 1, c->st)));
     }
@@ -715,7 +725,7 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
   // Rayleigh-Ritz matrix Hs = V W^T kept with leading dimension ms and updated by columns
   {
     Scope sc(c, "davidson_rr", 2.0 * m * (double)dim * sizeof(T), 2.0 * m * m * (double)dim);
-    CK((gemm<T, double>(false, true, m, m, (int)dim, 1.0, V, dim, W, dim, 0.0, Hs, ms, 0, c->st)));
+    CK(tn_product<T>(c, m, m, dim, V, dim, W, dim, Hs, ms));
     CK(symmetrize(m, Hs, ms, c->st));
   }
   int it = 0;
@@ -798,7 +808,7 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
       CK(cudaMemcpyAsync(W, S2, sizeof(T) * kp * dim, cudaMemcpyDeviceToDevice, c->st));
       m = kp;
       Scope sc(c, "davidson_rr", 2.0 * m * (double)dim * sizeof(T), 2.0 * m * m * (double)dim);
-      CK((gemm<T, double>(false, true, m, m, (int)dim, 1.0, V, dim, W, dim, 0.0, Hs, ms, 0, c->st)));
+      CK(tn_product<T>(c, m, m, dim, V, dim, W, dim, Hs, ms));
       CK(symmetrize(m, Hs, ms, c->st));
     }
     // CGS2 against V, dropping directions that lose all but 1e-8 of their norm
@@ -812,7 +822,7 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
     // cancellation one pass already leaves the rounding level of the data
     bool cancelled = false;
     for (int pass = 0; pass < 2; ++pass) {
-      CK((gemm<T, double>(false, true, m, nt, (int)dim, 1.0, V, dim, Tt, dim, 0.0, Cm, nt, 0, c->st)));
+      CK(tn_product<T>(c, m, nt, dim, V, dim, Tt, dim, Cm, nt));
       CK((convert<double, T>((long)m * nt, Cm, Cmt, c->st)));
       CK((gemm<T, T>(true, false, nt, (int)dim, m, -1.0, Cmt, nt, V, dim, 1.0, Tt, dim, 1, c->st)));
       CK(row_norms2<T>(nt, dim, Tt, nrm, c->st));
@@ -850,7 +860,7 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
     // CholQR2 among the new directions; a failing pivot drops that direction
     for (int pass = 0; pass < 2; ++pass) {
       while (true) {
-        CK((gemm<T, double>(false, true, nt, nt, (int)dim, 1.0, Tt, dim, Tt, dim, 0.0, Sg, nt, 0, c->st)));
+        CK(tn_product<T>(c, nt, nt, dim, Tt, dim, Tt, dim, Sg, nt));
         CK(symmetrize(nt, Sg, nt, c->st));
         CK(cholesky_inverse(nt, Sg, nt, Linv, info, c->st));
         int hinfo = 0;
@@ -876,8 +886,7 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
     {
       Scope sc(c, "davidson_rr", (m + 2.0 * nt) * (double)dim * sizeof(T),
                2.0 * (m + nt) * nt * (double)dim);
-      CK((gemm<T, double>(false, true, m + nt, nt, (int)dim, 1.0, V, dim, W + (long)m * dim, dim,
-                          0.0, Hs + m, ms, 0, c->st)));
+      CK(tn_product<T>(c, m + nt, nt, dim, V, dim, W + (long)m * dim, dim, Hs + m, ms));
       CK(mirror_new(Hs, ms, m, m + nt, c->st));
     }
     m += nt;

@@ -304,14 +304,19 @@ __global__ void precond_diag_kernel(int n_occ, int n_pw, const T* R, const doubl
   const long dim = (long)n_occ * n_pw;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = blockIdx.y, t = blockIdx.z;
-  if (j >= n_pw) return;
   const int i = which[t];
-  // d - theta = 1/2|G|^2 + (V(0) + Delta - eps_v - theta); the bracket is one value per block
-  const T c = (T)(v0 + shift - eps[v] - theta[i]);
-  T den = g2h[j] + c;
+  // d - theta = 1/2|G|^2 + (V(0) + Delta - eps_v - theta): the bracket is one value per block
+  __shared__ T cs;
+  if (threadIdx.x == 0) cs = (T)(v0 + shift - eps[v] - theta[i]);
+  __syncthreads();
+  if (j >= n_pw) return;
+  T den = g2h[j] + cs;
   if (den < (T)0.1) den = (T)0.1;
   const long e = (long)v * n_pw + j;
-  out[t * dim + e] = (j == 1) ? (T)0 : R[(long)i * dim + e] / den;
+  T val;
+  if constexpr (sizeof(T) == 4) val = __fdividef(R[(long)i * dim + e], den);   // a preconditioner: fast division
+  else val = R[(long)i * dim + e] / den;
+  out[t * dim + e] = (j == 1) ? (T)0 : val;
 }
 template <typename T>
 cudaError_t precond_diag(int k, int n_occ, int n_pw, const T* R, const double* theta,
