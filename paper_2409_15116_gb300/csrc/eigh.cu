@@ -157,9 +157,9 @@ __global__ void __launch_bounds__(512) eigh_lowest_kernel(int m, int k, const do
   }
   tnorm = fmax(fabs(gl), fabs(gu));
   const R pivmin = Tol::pivtiny + Tol::tiny * tnorm * tnorm;
-  // multisection: warp w brackets eigenvalues j = w, w + nw, ...; its 32 lanes evaluate the
-  // Sturm count at 32 interior points of the current bracket, which shrinks 33-fold a step
-  {
+  if constexpr (sizeof(R) == 4) {
+    // multisection: warp w brackets eigenvalues j = w, w + nw, ...; its 32 lanes evaluate the
+    // Sturm count at 32 interior points of the current bracket, which shrinks 33-fold a step
     const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     for (int j = wid; j < k; j += nw) {
       R lo = gl - 50 * Tol::eps * tnorm - Tol::tiny, hi = gu + 50 * Tol::eps * tnorm + Tol::tiny;
@@ -174,6 +174,18 @@ __global__ void __launch_bounds__(512) eigh_lowest_kernel(int m, int k, const do
         lo = nlo; hi = nhi;
       }
       if (lane == 0) lam[j] = (R)0.5 * (lo + hi);
+    }
+  } else {
+    // bisection, one thread per eigenvalue (FP64 runs at a small fraction of the FP32 rate,
+    // so every Sturm evaluation counts)
+    for (int j = tid; j < k; j += nt) {
+      R lo = gl - 50 * Tol::eps * tnorm - Tol::tiny, hi = gu + 50 * Tol::eps * tnorm + Tol::tiny;
+      for (int it = 0; it < 200 && hi - lo > Tol::eps * fmax(fabs(lo), fabs(hi)) + Tol::tiny; ++it) {
+        const R mid = (R)0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (sturm_count(m, d, e2, mid, pivmin) > j) hi = mid; else lo = mid;
+      }
+      lam[j] = (R)0.5 * (lo + hi);
     }
   }
   __syncthreads();
@@ -288,7 +300,9 @@ __global__ void __launch_bounds__(512) eigh_lowest_kernel(int m, int k, const do
 
 // k lowest eigenpairs of the symmetric m x m matrix A (lda): eigenvalues ascending in w[0..k),
 // eigenvectors as the columns of V (row-major m x k). work: at least 4*m*k + 2*k doubles.
-// single: single-precision arithmetic (double input and outputs).
+// single: single-precision Householder, bisection and inverse iteration, then the
+// eigenvalues refined in double as Rayleigh quotients of the computed vectors against A
+// (double input and outputs; the values come out accurate to double precision).
 template <typename R>
 static cudaError_t launch_eigh(int m, int k, const double* A, long lda, double* work, double* V, double* w,
                                int* info, cudaStream_t st) {
@@ -310,12 +324,36 @@ static cudaError_t launch_eigh(int m, int k, const double* A, long lda, double* 
   return cudaGetLastError();
 }
 
+// theta_j = v_j^T A v_j / v_j^T v_j in double for the columns of V (row-major m x k): one
+// CTA per eigenpair. With single-precision eigenvectors (error ~1e-6) the refined values
+// are accurate to second order, i.e. to double precision.
+__global__ void rayleigh_refine_kernel(int m, int k, const double* __restrict__ A, long lda,
+                                       const double* __restrict__ V, double* __restrict__ w) {
+  __shared__ double red[32];
+  const int j = blockIdx.x;
+  double num = 0, den = 0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double vi = V[(long)i * k + j];
+    double av = 0;
+    for (int l = 0; l < m; ++l) av += A[(long)i * lda + l] * V[(long)l * k + j];
+    num += vi * av;
+    den += vi * vi;
+  }
+  num = blk_sum(num, red);
+  den = blk_sum(den, red);
+  if (threadIdx.x == 0) w[j] = num / den;
+}
+
 cudaError_t eigh_lowest(int m, int k, const double* A, long lda, double* work, double* V, double* w,
                         int* info, bool single, cudaStream_t st) {
   if (m <= 0 || k <= 0) return cudaSuccess;
   if (m > EIGH_MAX || k > EIGH_KMAX || k > m) return cudaErrorInvalidValue;
-  return single ? launch_eigh<float>(m, k, A, lda, work, V, w, info, st)
-                : launch_eigh<double>(m, k, A, lda, work, V, w, info, st);
+  if (!single) return launch_eigh<double>(m, k, A, lda, work, V, w, info, st);
+  cudaError_t e = launch_eigh<float>(m, k, A, lda, work, V, w, info, st);
+  if (e != cudaSuccess) return e;
+  rayleigh_refine_kernel<<<k, 128, 0, st>>>(m, k, A, lda, V, w);
+  note_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace bse

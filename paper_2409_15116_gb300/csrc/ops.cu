@@ -242,22 +242,21 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return v;
 }
 
-// R_i = LX_i - theta_i X_i and ||R_i||^2. Arithmetic in the data precision (per-thread
-// partial sums of a few dozen terms), block and grid sums in double.
+// R_i = LX_i - theta_i X_i (data precision) and ||R_i||^2 accumulated in double
 template <typename T>
 __global__ void residual_kernel(long dim, const T* X, const T* LX, const double* theta, T* R,
                                 double* norms2) {
   __shared__ double sh[32];
   const int i = blockIdx.y;
   const T th = (T)theta[i];
-  T acc = 0;
+  double acc = 0;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < dim; e += (long)gridDim.x * blockDim.x) {
     const T r = fma(-th, X[i * dim + e], LX[i * dim + e]);
     R[i * dim + e] = r;
-    acc = fma(r, r, acc);
+    acc = fma((double)r, (double)r, acc);
   }
-  const double tot = block_sum((double)acc, sh);
-  if (threadIdx.x == 0) atomicAdd(norms2 + i, tot);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) atomicAdd(norms2 + i, acc);
 }
 template <typename T>
 cudaError_t residuals(int k, long dim, const T* X, const T* LX, const double* theta, T* R,
@@ -275,13 +274,13 @@ template <typename T>
 __global__ void row_norms2_kernel(long dim, const T* X, double* norms2) {
   __shared__ double sh[32];
   const int i = blockIdx.y;
-  T acc = 0;
+  double acc = 0;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < dim; e += (long)gridDim.x * blockDim.x) {
-    const T x = X[i * dim + e];
+    const double x = (double)X[i * dim + e];
     acc = fma(x, x, acc);
   }
-  const double tot = block_sum((double)acc, sh);
-  if (threadIdx.x == 0) atomicAdd(norms2 + i, tot);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) atomicAdd(norms2 + i, acc);
 }
 template <typename T>
 cudaError_t row_norms2(int k, long dim, const T* X, double* norms2, cudaStream_t st) {
