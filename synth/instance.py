@@ -338,6 +338,9 @@ CONFIGS = {
     # small profiling case of the same family: 48^3, 64 orbitals, 128 PDEP (~1 GB of fields)
     "small": lambda s=None: make_localized(8 if s is None else s, 20.0 * 48 / 72, 48, 64, 2.5, 128,
                                            name="small-L13.3-N48-occ64"),
+    # transform profiling case on the medium grid: 72^3, 32 orbitals, 64 PDEP (~1.5 GB of fields)
+    "grid72": lambda s=None: make_localized(10 if s is None else s, 20.0, 72, 32, 2.5, 64,
+                                            name="grid72-L20-N72-occ32"),
     # operator profiling case with the medium orbital count on a 32^3 grid (~3 GB of fields)
     "op256": lambda s=None: make_localized(9 if s is None else s, 20.0 * 32 / 72, 32, 256, 2.5, 512,
                                            name="op256-L8.9-N32-occ256"),
