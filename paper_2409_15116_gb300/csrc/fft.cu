@@ -402,18 +402,25 @@ __device__ __forceinline__ void dft_any(C* v, int sign, const C* tw) {
   else Dft<C, R>::run(v, sign);
 }
 
-// line buffer addressing: element q of line l at l * LS + q + q / 16 (odd LS)
+// Plane-kernel line addressing: element q of line l at l * PLS + q + q / 32, with an odd
+// line stride PLS. Stages between shared buffers run with consecutive lanes on consecutive
+// lines (LF: lines fast), so every such access steps by PLS or by one element and stays
+// free of bank conflicts; only a stage that reads or writes global memory runs with
+// consecutive lanes along the line, for coalescing. (A bank-conflict count of the stages'
+// access patterns over candidate paddings picked this layout.)
+template <int N> struct PPad { static constexpr int LS = (N + (N >> 5) + 1) | 1; };
 template <int N>
-__device__ __forceinline__ int lidx(int l, int q) { return l * Pad<N>::LS + q + (q >> 4); }
+__device__ __forceinline__ int lidx(int l, int q) { return l * PPad<N>::LS + q + (q >> 5); }
 
 // One Stockham stage of radix R over n_lines lines of length N, Ns = product of the
 // earlier radices. Load / store go through functors ld(line, q) and st(line, q, value).
-template <typename C, int N, int R, typename LD, typename ST>
+template <typename C, int N, int R, bool LF, typename LD, typename ST>
 __device__ __forceinline__ void pstage(int Ns, int sign, int n_lines, const C* tw, LD ld, ST st) {
   constexpr int NB = N / R;
   const int step = N / (Ns * R);
   for (int e = threadIdx.x; e < n_lines * NB; e += blockDim.x) {
-    const int i = e / NB, j = e - i * NB;
+    int i, j;
+    if (LF) { j = e / n_lines; i = e - j * n_lines; } else { i = e / NB; j = e - i * NB; }
     const int k = j % Ns;
     C v[R];
 #pragma unroll
@@ -431,7 +438,7 @@ template <typename T, int N>
 constexpr size_t plane_smem() {
   // column buffer A [NX <= N/2 + 1 slots] + (column buffer B | row plane P) + twiddles + slots
   constexpr int NXM = N / 2 + 1;
-  return (size_t)(NXM * Pad<N>::LS + N * Pad<N>::LS + N) * sizeof(cplx<T>) + (size_t)N * sizeof(int);
+  return (size_t)(NXM * PPad<N>::LS + N * PPad<N>::LS + N) * sizeof(cplx<T>) + (size_t)N * sizeof(int);
 }
 
 // inverse: I1[g][z][.] (z-transformed columns) -> grid plane (g, z); forward: the reverse.
@@ -444,9 +451,9 @@ __global__ void __launch_bounds__(256) sph_plane_kernel(cplx<T>* __restrict__ I1
   constexpr int NXM = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* colA = reinterpret_cast<C*>(smem_raw);          // [NXM][LS]
-  C* colB = colA + NXM * Pad<N>::LS;                 // [NXM][LS], shares space with P
+  C* colB = colA + NXM * PPad<N>::LS;                // [NXM][LS], shares space with P
   C* P = colB;                                       // [N][LS]
-  C* tw = P + N * Pad<N>::LS;
+  C* tw = P + N * PPad<N>::LS;
   int* slot = reinterpret_cast<int*>(tw + N);        // slot of x in the band, -1 outside
   load_twiddles<C, N>(tw, table, sign);
   for (int x = threadIdx.x; x < N; x += blockDim.x) slot[x] = -1;
@@ -457,39 +464,39 @@ __global__ void __launch_bounds__(256) sph_plane_kernel(cplx<T>* __restrict__ I1
   C* Gp = grid + gz * (long)N * N;
   const int nx = m.NX;
   if (INV) {
-    for (int e = threadIdx.x; e < nx * Pad<N>::LS; e += blockDim.x) colA[e] = cmk<C>(0, 0);
+    for (int e = threadIdx.x; e < nx * PPad<N>::LS; e += blockDim.x) colA[e] = cmk<C>(0, 0);
     __syncthreads();
     for (int c = threadIdx.x; c < m.NC; c += blockDim.x) colA[lidx<N>(m.cxi[c], m.cy[c])] = I1r[c];
     __syncthreads();
     // y lines of the band: A -> B -> A
-    pstage<C, N, R0>(1, sign, nx, tw, [&](int l, int q) { return colA[lidx<N>(l, q)]; },
-                     [&](int l, int q, C v) { colB[lidx<N>(l, q)] = v; });
+    pstage<C, N, R0, true>(1, sign, nx, tw, [&](int l, int q) { return colA[lidx<N>(l, q)]; },
+                           [&](int l, int q, C v) { colB[lidx<N>(l, q)] = v; });
     __syncthreads();
-    pstage<C, N, R1>(R0, sign, nx, tw, [&](int l, int q) { return colB[lidx<N>(l, q)]; },
-                     [&](int l, int q, C v) { colA[lidx<N>(l, q)] = v; });
+    pstage<C, N, R1, true>(R0, sign, nx, tw, [&](int l, int q) { return colB[lidx<N>(l, q)]; },
+                           [&](int l, int q, C v) { colA[lidx<N>(l, q)] = v; });
     __syncthreads();
     // x lines: the first stage reads the band from the column buffer (zero outside it),
     // the second writes the plane to global memory
-    pstage<C, N, R0>(1, sign, N, tw,
-                     [&](int y, int x) { const int s = slot[x]; return s >= 0 ? colA[lidx<N>(s, y)] : cmk<C>(0, 0); },
-                     [&](int y, int x, C v) { P[lidx<N>(y, x)] = v; });
+    pstage<C, N, R0, true>(1, sign, N, tw,
+                           [&](int y, int x) { const int s = slot[x]; return s >= 0 ? colA[lidx<N>(s, y)] : cmk<C>(0, 0); },
+                           [&](int y, int x, C v) { P[lidx<N>(y, x)] = v; });
     __syncthreads();
-    pstage<C, N, R1>(R0, sign, N, tw, [&](int y, int x) { return P[lidx<N>(y, x)]; },
-                     [&](int y, int x, C v) { Gp[y * N + x] = v; });
+    pstage<C, N, R1, false>(R0, sign, N, tw, [&](int y, int x) { return P[lidx<N>(y, x)]; },
+                            [&](int y, int x, C v) { Gp[y * N + x] = v; });
   } else {
     // x lines: the first stage reads the plane from global memory, the second keeps the band
-    pstage<C, N, R0>(1, sign, N, tw, [&](int y, int x) { return Gp[y * N + x]; },
-                     [&](int y, int x, C v) { P[lidx<N>(y, x)] = v; });
+    pstage<C, N, R0, false>(1, sign, N, tw, [&](int y, int x) { return Gp[y * N + x]; },
+                            [&](int y, int x, C v) { P[lidx<N>(y, x)] = v; });
     __syncthreads();
-    pstage<C, N, R1>(R0, sign, N, tw, [&](int y, int x) { return P[lidx<N>(y, x)]; },
-                     [&](int y, int x, C v) { const int s = slot[x]; if (s >= 0) colA[lidx<N>(s, y)] = v; });
+    pstage<C, N, R1, true>(R0, sign, N, tw, [&](int y, int x) { return P[lidx<N>(y, x)]; },
+                           [&](int y, int x, C v) { const int s = slot[x]; if (s >= 0) colA[lidx<N>(s, y)] = v; });
     __syncthreads();
     // y lines of the band: A -> B -> A
-    pstage<C, N, R0>(1, sign, nx, tw, [&](int l, int q) { return colA[lidx<N>(l, q)]; },
-                     [&](int l, int q, C v) { colB[lidx<N>(l, q)] = v; });
+    pstage<C, N, R0, true>(1, sign, nx, tw, [&](int l, int q) { return colA[lidx<N>(l, q)]; },
+                           [&](int l, int q, C v) { colB[lidx<N>(l, q)] = v; });
     __syncthreads();
-    pstage<C, N, R1>(R0, sign, nx, tw, [&](int l, int q) { return colB[lidx<N>(l, q)]; },
-                     [&](int l, int q, C v) { colA[lidx<N>(l, q)] = v; });
+    pstage<C, N, R1, true>(R0, sign, nx, tw, [&](int l, int q) { return colB[lidx<N>(l, q)]; },
+                           [&](int l, int q, C v) { colA[lidx<N>(l, q)] = v; });
     __syncthreads();
     for (int c = threadIdx.x; c < m.NC; c += blockDim.x) I1r[c] = colA[lidx<N>(m.cxi[c], m.cy[c])];
   }
