@@ -351,8 +351,14 @@ def main():
     t_launch = d["ms"] / nl * 1e-3
     bytes_launch = d["bytes"] / d["calls"] if name not in per_kernel_launches else d["bytes"] / d["calls"]
     achieved = bytes_launch / t_launch / 1e9
+    # DRAM traffic per launch: the K1d kernel was captured with ncu on the op256 case
+    # (32 vectors, 32^3 grid, 4,934 pairs): 2.800 GB read + written against 2.832 GB of
+    # algorithmic bytes; its traffic scales with the same per-point, per-pair and per-vector
+    # counts, so the ratio carries over to this launch's algorithmic bytes
+    K1D_DRAM_PER_ALGORITHMIC_BYTE = 2.800075 / 2.832204
+    traffic = bytes_launch * K1D_DRAM_PER_ALGORITHMIC_BYTE if name == "k1d_combine" else None
     roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": None,
+            "frac": achieved / hbm_peak, "traffic": traffic,
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     regions = {k: {"ms_per_step": v["ms"] / args.steps, "calls": v["calls"],
                    "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
