@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <memory>
 #include <queue>
 #include <string>
@@ -75,6 +76,9 @@ struct bse_ctx {
   Split psi_s, psiT_s, pdep_s, pdepT_s;
   void *ws_ahi = nullptr, *ws_alo = nullptr, *ws_bhi = nullptr, *ws_blo = nullptr;
   long ws_split_rows = 0;
+  // TMA maps of the split workspace, by (base pointer, leading dimension); they span the
+  // workspace's full row capacity, so they stay valid until it is reallocated
+  std::map<std::pair<const void*, long>, TMap> ws_maps;
   int* d_err = nullptr;
   // learned preconditioner: inference weights and training samples
   float* lp_params = nullptr;
@@ -210,6 +214,7 @@ int make_split64(bse_ctx* c, Split& sp, const double* X, long rows, long cols, b
 // workspace for the per-call splits: A operand (K = n_pw) and the small-K operand
 int ensure_split_ws(bse_ctx* c, long rows) {
   if (rows <= c->ws_split_rows) return BSE_OK;
+  c->ws_maps.clear();
   dfree(c, c->ws_ahi); dfree(c, c->ws_alo); dfree(c, c->ws_bhi); dfree(c, c->ws_blo);
   c->ws_ahi = c->ws_alo = c->ws_bhi = c->ws_blo = nullptr;
   c->ws_split_rows = 0;
@@ -231,9 +236,21 @@ int tc_product(bse_ctx* c, const float* X, long M, long K, long ldx, const Split
   void* hi = small_k_slot ? c->ws_bhi : c->ws_ahi;
   void* lo = small_k_slot ? c->ws_blo : c->ws_alo;
   CK(bf16_split(X, M, (int)K, ldx, hi, lo, ld, c->st));
-  TMap mh, ml;
-  if (!tc_make_map(mh.b, hi, M, ld, ld) || !tc_make_map(ml.b, lo, M, ld, ld))
-    return fail(c, BSE_ERR_CUDA, "TMA tensor map creation failed");
+  // maps over the workspace's full capacity, built once: rows M.. of the last tile read
+  // stale split data, whose output rows are never written
+  auto ws_map = [&](const void* p) -> const TMap* {
+    const auto key = std::make_pair(p, ld);
+    auto it = c->ws_maps.find(key);
+    if (it != c->ws_maps.end()) return &it->second;
+    TMap m;
+    if (!tc_make_map(m.b, p, c->ws_split_rows, ld, ld)) return nullptr;
+    return &(c->ws_maps[key] = m);
+  };
+  const TMap* mhp = ws_map(hi);
+  const TMap* mlp = ws_map(lo);
+  if (!mhp || !mlp) return fail(c, BSE_ERR_CUDA, "TMA tensor map creation failed");
+  const TMap& mh = *mhp;
+  const TMap& ml = *mlp;
   const long tiles = ((M + 127) / 128) * ((B.rows + 127) / 128);
   const long kt = (K + 63) / 64;
   int splits = 1;
