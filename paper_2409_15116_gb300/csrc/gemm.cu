@@ -172,11 +172,14 @@ static cudaError_t dispatch_t(bool at, bool bt, int M, int N, int K, double alph
 //
 // ts_tn:  C (M x N, double) = alpha A B^T + beta C with A M x K, B N x K, N <= 32 and K
 //         in the millions (Gram, Rayleigh-Ritz and CGS coefficient matrices). A CTA takes
-//         a 2048-long stretch of K and a 64-row tile of A, streamed through a four-stage
-//         cp.async ring in 32-wide chunks; each warp computes the whole 64 x 32 tile on
-//         its own 4-wide slice of every chunk (lane: 8 x 8 outputs as packed FP32 pairs),
-//         so every accumulator sums 256 products in FP32; the eight warp partials are
-//         added in double and accumulated into C with double-precision atomics.
+//         a stretch of K (2048 by default) and a BM-row tile of A, streamed through a
+//         three-stage cp.async ring. Its eight warps are RG row groups x KG k groups: a warp
+//         owns an (8 LR) x (4 LC) block of C over its share of every staged chunk (KW
+//         consecutive k), a lane an LR x LC block. The packed FP32x2 accumulators pair
+//         consecutive k (even k in .x, odd k in .y), so both operands of every packed FMA
+//         are adjacent words of one 16-byte shared-memory load and no register moves are
+//         needed. The k-group partials are added in shared memory and accumulated into C
+//         with double-precision atomics.
 // ts_nn:  C (M x N) = alpha op(A) B + beta C with op(A) M x K small (K <= 256) and N in the
 //         millions (CGS update, Cholesky-QR, Ritz vectors, restart). op(A) sits in shared
 //         memory; a thread owns four adjacent columns and a band of up to 16 rows,
@@ -184,14 +187,13 @@ static cudaError_t dispatch_t(bool at, bool bt, int M, int N, int K, double alph
 // ---------------------------------------------------------------------------------
 namespace {
 
-constexpr int TS_KS = 2048;    // K per CTA (ts_tn)
-constexpr int TS_KC = 32;      // K per staged chunk
-constexpr int TS_STAGES = 4;
+constexpr int TN_KS = 2048;    // K per CTA (ts_tn)
+constexpr int TN_STAGES = 3;
 
-// staged chunk row: 32 floats in eight 16-byte groups, group g stored at g ^ (row >> SWS) % 8,
-// so that lanes reading the same group of different rows hit distinct banks
-template <int SWS>
-__device__ __forceinline__ int ts_off(int row, int g) { return row * TS_KC + ((g ^ ((row >> SWS) & 7)) << 2); }
+// staged row of G 16-byte groups, group g stored at g ^ (row % 8): eight consecutive rows
+// read at the same group hit eight distinct bank quads
+template <int G>
+__device__ __forceinline__ int tn_off(int row, int g) { return row * (4 * G) + ((g ^ (row & 7)) << 2); }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -199,104 +201,143 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool va
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
 }
 
-// BM rows of A per CTA (64 or 32); SYM: B is A (a Gram matrix, M = N <= 32), staged once
-template <int BM, bool SYM>
-__global__ void __launch_bounds__(256, 2) ts_gemm_tn_kernel(int M, int N, long K, double alpha,
-                                                           const float* __restrict__ A, long lda,
-                                                           const float* __restrict__ B, long ldb,
-                                                           double* __restrict__ C, long ldc) {
-  static_assert(BM == 64 || (BM == 32), "row tile");
-  static_assert(!SYM || BM == 32, "Gram tile");
-  constexpr int RI = BM / 8;                         // rows of A per lane
-  constexpr int SWS = (BM == 64) ? 3 : 2;
-  constexpr int ROWS = SYM ? BM : BM + 32;           // staged rows per chunk
-  constexpr int STAGE = ROWS * TS_KC;                // floats per stage
-  constexpr int PIECES = ROWS * 8 / 256;             // 16-byte copies per thread per chunk
+// tile shape of one instantiation
+template <int LR, int LC, int RG, bool SYM>
+struct TnShape {
+  static constexpr int WR = 8 * LR, BN = 4 * LC, BM = RG * WR, KG = 8 / RG;
+  // k per warp per chunk: 16, or 8 where a 16-wide share would make the ring too large for
+  // two CTAs per SM
+  static constexpr int ROWS = SYM ? BM : BM + BN;
+  static constexpr int KW = (ROWS * 16 * KG * 4 * TN_STAGES <= 110 * 1024) ? 16 : 8;
+  static constexpr int KC = KW * KG;                 // k per chunk
+  static constexpr int G = KC / 4;                   // 16-byte groups per staged row
+  static constexpr int STAGE = ROWS * KC;            // floats per stage
+  static constexpr int PIECES = ROWS * G;            // 16-byte copies per chunk
+  static constexpr size_t RING = (size_t)TN_STAGES * STAGE * sizeof(float);
+  static constexpr size_t RED = (size_t)KG * BM * BN * sizeof(float);
+  static constexpr size_t SMEM = RING > RED ? RING : RED;
+  static_assert(RG * KG == 8 && PIECES % 256 == 0 && G >= 8, "tile shape");
+  static_assert(!SYM || BM == BN, "Gram tile");
+};
+
+// acc += (a.x b.x, a.y b.y) + (a.z b.z, a.w b.w): four consecutive k in two packed FMAs
+__device__ __forceinline__ void tn_mac(float2& acc, const float4& a, const float4& b) {
+  acc = __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y), acc);
+  acc = __ffma2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w), acc);
+}
+
+template <int LR, int LC, int RG, bool SYM>
+__global__ void __launch_bounds__(256, 2) ts_tn_kernel(int M, int N, long K, long ks, double alpha,
+                                                      const float* __restrict__ A, long lda,
+                                                      const float* __restrict__ B, long ldb,
+                                                      double* __restrict__ C, long ldc) {
+  using S = TnShape<LR, LC, RG, SYM>;
   extern __shared__ __align__(16) float ts_smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const long i0 = (long)blockIdx.y * BM;
-  const long kbeg = (long)blockIdx.x * TS_KS;
-  const long kend = min(K, kbeg + TS_KS);
-  const int nch = (int)((kend - kbeg + TS_KC - 1) / TS_KC);
+  const int rg = warp / S::KG, kg = warp % S::KG;
+  const int ib = lane >> 2, jb = lane & 3;
+  const long i0 = (long)blockIdx.x * S::BM;
+  const long kbeg = (long)blockIdx.y * ks;
+  const long kend = min(K, kbeg + ks);
+  const int nch = (int)((kend - kbeg + S::KC - 1) / S::KC);
+  // staging: thread tid copies group pg of rows prow + RPP q (q = 0 .. PIECES / 256 - 1);
+  // whether a round q holds rows of A or of B is known at compile time
+  constexpr int RPP = 256 / S::G;
+  static_assert(RPP % 8 == 0 && (SYM || S::BM % RPP == 0), "staging rounds");
+  const int prow = tid / S::G, pg = tid % S::G;
+  const int dst0 = prow * (4 * S::G) + ((pg ^ (prow & 7)) << 2);
+  const float* srcA = A + (i0 + prow) * lda + 4 * pg;
+  const float* srcB = B + 4 * pg;
+  const long rowsA = (long)M - i0 - prow;            // round q of A is valid while q RPP < rowsA
   auto issue = [&](int ch) {
-    float* st = ts_smem + (ch % TS_STAGES) * STAGE;
+    float* st = ts_smem + (ch % TN_STAGES) * S::STAGE + dst0;
+    const long kc = (long)ch * S::KC;
+    const bool kok = kbeg + kc + 4 * pg < kend;
 #pragma unroll
-    for (int q = 0; q < PIECES; ++q) {
-      const int e = tid + 256 * q;
-      const int row = e >> 3, g = e & 7;
-      const long k = kbeg + (long)ch * TS_KC + 4 * g;
-      const float* src;
-      bool ok;
-      if (row < BM) {
-        const long i = i0 + row;
-        ok = (i < M) && (k < kend);
-        src = ok ? A + i * lda + k : A;
+    for (int q = 0; q < S::PIECES / 256; ++q) {
+      if (SYM || q * RPP < S::BM) {
+        const bool ok = kok && (q * RPP < rowsA);
+        cp_async16(st + q * RPP * 4 * S::G, ok ? srcA + (long)q * RPP * lda + kbeg + kc : A, ok);
       } else {
-        const int j = row - BM;
-        ok = (j < N) && (k < kend);
-        src = ok ? B + (long)j * ldb + k : B;
+        const int j = prow + q * RPP - S::BM;
+        const bool ok = kok && (j < N);
+        cp_async16(st + q * RPP * 4 * S::G, ok ? srcB + (long)j * ldb + kbeg + kc : B, ok);
       }
-      cp_async16(st + ts_off<SWS>(row, g), src, ok);
     }
   };
 #pragma unroll
-  for (int s0 = 0; s0 < TS_STAGES - 1; ++s0) {
+  for (int s0 = 0; s0 < TN_STAGES - 1; ++s0) {
     if (s0 < nch) issue(s0);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
-  const int ib = lane >> 2, jb = lane & 3;
-  float2 acc[RI][4];
+  // operand loads: offsets of this lane's first A row and first two B rows, per k step;
+  // further rows are 8 apart and keep the same swizzle, so they are immediate offsets
+  constexpr int NQ = S::KW / 4;
+  int offa[NQ], offb[2][NQ];
 #pragma unroll
-  for (int i = 0; i < RI; ++i)
+  for (int q = 0; q < NQ; ++q) {
+    const int g = kg * NQ + q;
+    offa[q] = (rg * S::WR + ib) * (4 * S::G) + ((g ^ ib) << 2);
+    offb[0][q] = jb * (4 * S::G) + ((g ^ jb) << 2);
+    offb[1][q] = (4 + jb) * (4 * S::G) + ((g ^ (4 + jb)) << 2);
+  }
+  constexpr int ROW8 = 8 * 4 * S::G;                 // floats between rows r and r + 8
+  float2 acc[LR][LC];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (int r = 0; r < LR; ++r)
+#pragma unroll
+    for (int c = 0; c < LC; ++c) acc[r][c] = make_float2(0.f, 0.f);
   for (int ch = 0; ch < nch; ++ch) {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(TS_STAGES - 2) : "memory");
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(TN_STAGES - 2) : "memory");
     __syncthreads();
-    if (ch + TS_STAGES - 1 < nch) issue(ch + TS_STAGES - 1);
+    if (ch + TN_STAGES - 1 < nch) issue(ch + TN_STAGES - 1);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
-    const float* as = ts_smem + (ch % TS_STAGES) * STAGE;
-    const float* bs = SYM ? as : as + BM * TS_KC;
-    // this warp's four k values: group `warp` of every row
-    float2 bp[4][4];    // [k][j pair]
+    const float* as = ts_smem + (ch % TN_STAGES) * S::STAGE;
+    const float* bs = SYM ? as : as + S::BM * S::KC;
 #pragma unroll
-    for (int jp = 0; jp < 4; ++jp) {
-      const float4 u = *reinterpret_cast<const float4*>(bs + ts_off<SWS>(8 * jb + 2 * jp, warp));
-      const float4 v = *reinterpret_cast<const float4*>(bs + ts_off<SWS>(8 * jb + 2 * jp + 1, warp));
-      bp[0][jp] = make_float2(u.x, v.x);
-      bp[1][jp] = make_float2(u.y, v.y);
-      bp[2][jp] = make_float2(u.z, v.z);
-      bp[3][jp] = make_float2(u.w, v.w);
-    }
+    for (int q = 0; q < NQ; ++q) {
+      const float* aq = as + offa[q];
+      // the narrower operand stays in registers for the step, the other streams through
+      if constexpr (LR <= LC) {
+        float4 a[LR];
 #pragma unroll
-    for (int i = 0; i < RI; ++i) {
-      const float4 a = *reinterpret_cast<const float4*>(as + ts_off<SWS>(RI * ib + i, warp));
-      const float ak[4] = {a.x, a.y, a.z, a.w};
+        for (int r = 0; r < LR; ++r) a[r] = *reinterpret_cast<const float4*>(aq + r * ROW8);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const float2 ai = make_float2(ak[kk], ak[kk]);
+        for (int c = 0; c < LC; ++c) {
+          const float4 b = *reinterpret_cast<const float4*>(bs + offb[c & 1][q] + (c >> 1) * ROW8);
 #pragma unroll
-        for (int jp = 0; jp < 4; ++jp) acc[i][jp] = __ffma2_rn(ai, bp[kk][jp], acc[i][jp]);
+          for (int r = 0; r < LR; ++r) tn_mac(acc[r][c], a[r], b);
+        }
+      } else {
+        float4 b[LC];
+#pragma unroll
+        for (int c = 0; c < LC; ++c) b[c] = *reinterpret_cast<const float4*>(bs + offb[c & 1][q] + (c >> 1) * ROW8);
+#pragma unroll
+        for (int r = 0; r < LR; ++r) {
+          const float4 a = *reinterpret_cast<const float4*>(aq + r * ROW8);
+#pragma unroll
+          for (int c = 0; c < LC; ++c) tn_mac(acc[r][c], a, b[c]);
+        }
       }
     }
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
-  // eight warp partials -> double sums -> atomics
-  float* red = ts_smem;                              // [8][BM][32]
+  // k-group partials -> shared memory -> one double atomic per output
+  float* red = ts_smem;                              // [KG][BM][BN]
 #pragma unroll
-  for (int i = 0; i < RI; ++i)
+  for (int r = 0; r < LR; ++r)
 #pragma unroll
-    for (int jp = 0; jp < 4; ++jp)
-      *reinterpret_cast<float2*>(red + ((size_t)warp * BM + RI * ib + i) * 32 + 8 * jb + 2 * jp) = acc[i][jp];
+    for (int c = 0; c < LC; ++c)
+      red[((size_t)kg * S::BM + rg * S::WR + r * 8 + ib) * S::BN + c * 4 + jb] = acc[r][c].x + acc[r][c].y;
   __syncthreads();
-  for (int o = tid; o < BM * 32; o += 256) {
-    const int i = o >> 5, j = o & 31;
+  for (int o = tid; o < S::BM * S::BN; o += 256) {
+    const int i = o / S::BN, j = o % S::BN;
     if (i0 + i >= M || j >= N) continue;
-    double sum = 0.0;
+    float sum = 0.f;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) sum += (double)red[w * BM * 32 + o];
-    atomicAdd(C + (i0 + i) * ldc + j, alpha * sum);
+    for (int w = 0; w < S::KG; ++w) sum += red[w * S::BM * S::BN + o];
+    atomicAdd(C + (i0 + i) * ldc + j, alpha * (double)sum);
   }
 }
 
@@ -369,34 +410,50 @@ __global__ void __launch_bounds__(256) ts_gemm_nn_kernel(int M, long N, int K, d
 
 bool aligned(const void* p, size_t b) { return ((uintptr_t)p % b) == 0; }
 
-template <int BM, bool SYM>
+template <int LR, int LC, int RG, bool SYM>
 cudaError_t ts_tn_launch(int M, int N, long K, double alpha, const float* A, long lda, const float* B,
-                         long ldb, double* C, long ldc, cudaStream_t st) {
-  // the reduction area (8 x BM x 32 floats) and the staging ring, whichever is larger
-  constexpr size_t red = 8 * (size_t)BM * 32 * sizeof(float);
-  constexpr size_t ring = (size_t)TS_STAGES * (SYM ? BM : BM + 32) * TS_KC * sizeof(float);
-  constexpr size_t smem = red > ring ? red : ring;
+                         long ldb, double* C, long ldc, cudaStream_t st, long ks = TN_KS) {
+  using S = TnShape<LR, LC, RG, SYM>;
   static std::once_flag once;
   static cudaError_t once_st = cudaSuccess;
   cudaError_t e0 = once_status(once, once_st, [&] {
-    return cudaFuncSetAttribute(ts_gemm_tn_kernel<BM, SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(ts_tn_kernel<LR, LC, RG, SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)S::SMEM);
   });
   if (e0 != cudaSuccess) return e0;
-  dim3 grid((unsigned)((K + TS_KS - 1) / TS_KS), (unsigned)((M + BM - 1) / BM));
-  ts_gemm_tn_kernel<BM, SYM><<<grid, 256, smem, st>>>(M, N, K, alpha, A, lda, B, ldb, C, ldc); note_launch();
+  while ((K + ks - 1) / ks > 65535) ks *= 2;
+  dim3 grid((unsigned)((M + S::BM - 1) / S::BM), (unsigned)((K + ks - 1) / ks));
+  ts_tn_kernel<LR, LC, RG, SYM><<<grid, 256, S::SMEM, st>>>(M, N, K, ks, alpha, A, lda, B, ldb, C, ldc);
+  note_launch();
   return cudaGetLastError();
 }
 
-// C = alpha A B^T + beta C, A M x K, B N x K (both row-major), N <= 32
+// C = alpha A B^T + beta C, A M x K, B N x K (both row-major), N <= 32. The row tile is the
+// one of 32, 64 or 128 rows that pads M least (ties: the larger tile); the column tile is
+// 16 or 32 wide.
 cudaError_t ts_gemm_tn(int M, int N, long K, double alpha, const float* A, long lda, const float* B,
                        long ldb, double beta, double* C, long ldc, cudaStream_t st) {
   const long tot = (long)M * N;
   scale_matrix_kernel<double><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, C, ldc, beta); note_launch();
   if (K == 0) return cudaGetLastError();
-  if (M <= 32 && A == B && lda == ldb && M == N)
-    return ts_tn_launch<32, true>(M, N, K, alpha, A, lda, B, ldb, C, ldc, st);
-  if (M <= 32) return ts_tn_launch<32, false>(M, N, K, alpha, A, lda, B, ldb, C, ldc, st);
-  return ts_tn_launch<64, false>(M, N, K, alpha, A, lda, B, ldb, C, ldc, st);
+  if (A == B && lda == ldb && M == N && M <= 32) {
+    if (M <= 16) return ts_tn_launch<2, 4, 1, true>(M, N, K, alpha, A, lda, B, ldb, C, ldc, st);
+    return ts_tn_launch<4, 8, 1, true>(M, N, K, alpha, A, lda, B, ldb, C, ldc, st);
+  }
+  int bm = 128;
+  for (int cand : {64, 32}) {
+    const long pc = (M + cand - 1) / cand * (long)cand, pb = (M + bm - 1) / bm * (long)bm;
+    if (pc < pb) bm = cand;
+  }
+  if (N <= 16) {
+    if (M <= 16) return ts_tn_launch<2, 4, 1, false>(M, N, K, alpha, A, lda, B, ldb, C, ldc, st);
+    if (bm == 32) return ts_tn_launch<4, 4, 1, false>(M, N, K, alpha, A, lda, B, ldb, C, ldc, st);
+    if (bm == 64) return ts_tn_launch<8, 4, 1, false>(M, N, K, alpha, A, lda, B, ldb, C, ldc, st);
+    return ts_tn_launch<8, 4, 2, false>(M, N, K, alpha, A, lda, B, ldb, C, ldc, st);
+  }
+  if (bm == 32) return ts_tn_launch<4, 8, 1, false>(M, N, K, alpha, A, lda, B, ldb, C, ldc, st);
+  if (bm == 64) return ts_tn_launch<4, 8, 2, false>(M, N, K, alpha, A, lda, B, ldb, C, ldc, st);
+  return ts_tn_launch<4, 8, 4, false>(M, N, K, alpha, A, lda, B, ldb, C, ldc, st);
 }
 
 template <int MT>
