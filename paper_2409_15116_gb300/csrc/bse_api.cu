@@ -94,6 +94,7 @@ struct bse_ctx {
   cudaStream_t st = nullptr;
   std::string err = "no error";
   std::vector<double> g2p_h, eps_h, O_h;
+  std::vector<double> occw_h;  // per packed coordinate j: sum_v psi_v(j)^2 (occupied weight)
   std::vector<int32_t> pv_h, pw_h;
   double thr = 0;
   bool tau_ready = false;
@@ -718,6 +719,15 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
       const int j = jord[0][pos[v]];
       pq.push({Cand{dval(v, j), (long)v * c->n_pw + j}, v});
     }
+    // P_c acts on each orbital row alike, so (for the orthonormal orbitals the interface
+    // requires) the projected unit vector at coordinate j keeps 1 - sum_w psi_w(j)^2 of its
+    // squared norm in every row; orthogonalising against
+    // accepted vectors only lowers it. A candidate below the acceptance norm (0.1) by a
+    // margin beyond rounding, or at the pad coordinate, is rejected without device work.
+    {
+      const int jc = (int)(top.first.flat % c->n_pw);
+      if (jc == 1 || 1.0 - c->occw_h[jc] < 0.01 * (1.0 - 1e-3)) continue;
+    }
     T* x = V + (long)m * dim;
     CK(set_unit<T>(x, dim, top.first.flat, c->st));
     CA(project<T>(c, c->n_occ, x, pcbuf));
@@ -1064,6 +1074,9 @@ int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) 
   }
   UPLOAD(c->f, fh.data(), fh.size());
   UPLOAD(c->psi64, s->psi, npsi);
+  c->occw_h.assign(c->n_pw, 0.0);
+  for (int v = 0; v < c->n_occ; ++v)
+    for (int j = 0; j < c->n_pw; ++j) c->occw_h[j] += s->psi[(long)v * c->n_pw + j] * s->psi[(long)v * c->n_pw + j];
   UPLOAD(c->vloc64, s->v_loc, c->n3);
   if (c->n_pdep > 0) UPLOAD(c->pdep64, s->pdep, (long)c->n_pdep * c->n_pw);
   std::vector<double2> tw;
