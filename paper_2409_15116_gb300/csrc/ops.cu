@@ -242,21 +242,47 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return v;
 }
 
-// R_i = LX_i - theta_i X_i (data precision) and ||R_i||^2 accumulated in double
+// Per-thread sum of squares with the accuracy of double precision. For single precision
+// the square is split exactly into p + e (e = fma(x, x, -p)) and p is added with an
+// error-free two-sum whose rounding error joins e in a compensation term, so the work stays
+// in FP32 instructions (FP64 runs at a small fraction of the FP32 rate on this part). The
+// rounding-mode intrinsics keep the compiler from contracting the sums into FMAs.
+template <typename T>
+struct SqSum {
+  double s = 0.0;
+  __device__ __forceinline__ void add(T x) { s = fma((double)x, (double)x, s); }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct SqSum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float p = __fmul_rn(x, x);
+    const float e = __fmaf_rn(x, x, -p);
+    const float t = __fadd_rn(s, p);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    c = __fadd_rn(c, __fadd_rn(err, e));
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+};
+
+// R_i = LX_i - theta_i X_i (data precision) and ||R_i||^2 to double accuracy
 template <typename T>
 __global__ void residual_kernel(long dim, const T* X, const T* LX, const double* theta, T* R,
                                 double* norms2) {
   __shared__ double sh[32];
   const int i = blockIdx.y;
   const T th = (T)theta[i];
-  double acc = 0;
+  SqSum<T> acc;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < dim; e += (long)gridDim.x * blockDim.x) {
     const T r = fma(-th, X[i * dim + e], LX[i * dim + e]);
     R[i * dim + e] = r;
-    acc = fma((double)r, (double)r, acc);
+    acc.add(r);
   }
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) atomicAdd(norms2 + i, acc);
+  const double tot = block_sum(acc.get(), sh);
+  if (threadIdx.x == 0) atomicAdd(norms2 + i, tot);
 }
 template <typename T>
 cudaError_t residuals(int k, long dim, const T* X, const T* LX, const double* theta, T* R,
@@ -274,13 +300,11 @@ template <typename T>
 __global__ void row_norms2_kernel(long dim, const T* X, double* norms2) {
   __shared__ double sh[32];
   const int i = blockIdx.y;
-  double acc = 0;
-  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < dim; e += (long)gridDim.x * blockDim.x) {
-    const double x = (double)X[i * dim + e];
-    acc = fma(x, x, acc);
-  }
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) atomicAdd(norms2 + i, acc);
+  SqSum<T> acc;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < dim; e += (long)gridDim.x * blockDim.x)
+    acc.add(X[i * dim + e]);
+  const double tot = block_sum(acc.get(), sh);
+  if (threadIdx.x == 0) atomicAdd(norms2 + i, tot);
 }
 template <typename T>
 cudaError_t row_norms2(int k, long dim, const T* X, double* norms2, cudaStream_t st) {
@@ -300,29 +324,29 @@ template <typename T>
 __global__ void precond_diag_kernel(int n_occ, int n_pw, const T* R, const double* theta,
                                     const int* which, const T* g2h, const double* eps,
                                     double v0, double shift, T* out) {
+  // one CTA per (orbital row v, corrected vector t): d - theta = 1/2|G|^2 + (V(0) + Delta -
+  // eps_v - theta), the bracket one value per row
   const long dim = (long)n_occ * n_pw;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int v = blockIdx.y, t = blockIdx.z;
+  const int v = blockIdx.x, t = blockIdx.y;
   const int i = which[t];
-  // d - theta = 1/2|G|^2 + (V(0) + Delta - eps_v - theta): the bracket is one value per block
-  __shared__ T cs;
-  if (threadIdx.x == 0) cs = (T)(v0 + shift - eps[v] - theta[i]);
-  __syncthreads();
-  if (j >= n_pw) return;
-  T den = g2h[j] + cs;
-  if (den < (T)0.1) den = (T)0.1;
-  const long e = (long)v * n_pw + j;
-  T val;
-  if constexpr (sizeof(T) == 4) val = __fdividef(R[(long)i * dim + e], den);   // a preconditioner: fast division
-  else val = R[(long)i * dim + e] / den;
-  out[t * dim + e] = (j == 1) ? (T)0 : val;
+  const T cs = (T)(v0 + shift - eps[v] - theta[i]);
+  const T* r = R + (long)i * dim + (long)v * n_pw;
+  T* o = out + (long)t * dim + (long)v * n_pw;
+  for (int j = threadIdx.x; j < n_pw; j += blockDim.x) {
+    T den = g2h[j] + cs;
+    if (den < (T)0.1) den = (T)0.1;
+    T val;
+    if constexpr (sizeof(T) == 4) val = __fdividef(r[j], den);   // a preconditioner: fast division
+    else val = r[j] / den;
+    o[j] = (j == 1) ? (T)0 : val;
+  }
 }
 template <typename T>
 cudaError_t precond_diag(int k, int n_occ, int n_pw, const T* R, const double* theta,
                          const int* which, const T* g2h, const double* eps, double v0,
                          double shift, T* out, cudaStream_t st) {
   if (!k) return cudaSuccess;
-  dim3 grid(nblk(n_pw), n_occ, k);
+  dim3 grid(n_occ, k);
   precond_diag_kernel<T><<<grid, 256, 0, st>>>(n_occ, n_pw, R, theta, which, g2h, eps, v0, shift, out); note_launch();
   return cudaGetLastError();
 }
