@@ -273,7 +273,10 @@ cudaError_t tc_gemm_bf16x3(const void* mAh, const void* mAl, const void* mBh, co
   splits = kt_all > 0 ? (kt_all + kper - 1) / kper : 1;
   TcArgs a;
   a.M = M; a.N = N; a.K = K; a.kt_per_split = kper; a.alpha = (float)alpha; a.beta = (float)beta;
-  a.out = out; a.ldo = ldo; a.atomic = splits > 1 ? 1 : 0; a.err = err;
+  // beta = 1 (an update out += alpha A B^T) also goes through reductions: each element
+  // receives one FP32 add, the same value as a read-modify-write, without the epilogue
+  // waiting on loads of the old output
+  a.out = out; a.ldo = ldo; a.atomic = (splits > 1 || beta == 1.0) ? 1 : 0; a.err = err;
   if (splits > 1 && beta != 1.0) {
     // partial tiles are added atomically: pre-scale the output (beta = 0 clears it)
     cudaError_t e = (beta == 0.0) ? cudaSuccess : cudaErrorInvalidValue;
@@ -291,16 +294,22 @@ cudaError_t tc_gemm_bf16x3(const void* mAh, const void* mAl, const void* mBh, co
   return cudaGetLastError();
 }
 
-// x -> (hi, lo) bf16 with hi = RN(x), lo = RN(x - hi); columns [cols, ld_out) are zero
+// x -> (hi, lo) bf16 with hi = RN(x), lo = RN(x - hi); columns [cols, ld_out) are zero.
+// One CTA per row; a thread converts two adjacent columns and stores them as bf16 pairs
+// (ld_out is a multiple of 8, so every output row starts 16-byte aligned).
 __global__ void bf16_split_kernel(const float* __restrict__ X, long rows, int cols, long ld_in,
                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long ld_out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= ld_out) return;
-  for (long i = blockIdx.y; i < rows; i += gridDim.y) {
-    const float x = j < cols ? X[i * ld_in + j] : 0.f;
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    hi[i * ld_out + j] = h;
-    lo[i * ld_out + j] = __float2bfloat16_rn(x - __bfloat162float(h));
+  for (long i = blockIdx.x; i < rows; i += gridDim.x) {
+    const float* x = X + i * ld_in;
+    __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(hi + i * ld_out);
+    __nv_bfloat162* l2 = reinterpret_cast<__nv_bfloat162*>(lo + i * ld_out);
+    for (long j = 2 * threadIdx.x; j < ld_out; j += 2 * blockDim.x) {
+      const float x0 = j < cols ? x[j] : 0.f, x1 = j + 1 < cols ? x[j + 1] : 0.f;
+      const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+      const float2 hf = __bfloat1622float2(h);
+      h2[j >> 1] = h;
+      l2[j >> 1] = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+    }
   }
 }
 // same from an FP64 source
@@ -332,8 +341,9 @@ __global__ void bf16_split64_t_kernel(const double* __restrict__ X, long rows, i
 cudaError_t bf16_split(const float* X, long rows, int cols, long ld_in, void* hi, void* lo, long ld_out,
                        cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((ld_out + 255) / 256), (unsigned)(rows < 65535 ? rows : 65535));
-  bf16_split_kernel<<<grid, 256, 0, st>>>(X, rows, cols, ld_in, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, ld_out);
+  if (ld_out % 8 || ((uintptr_t)hi) % 16 || ((uintptr_t)lo) % 16) return cudaErrorInvalidValue;
+  const unsigned nb = (unsigned)(rows < 2147483647L ? rows : 2147483647L);
+  bf16_split_kernel<<<nb, 256, 0, st>>>(X, rows, cols, ld_in, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, ld_out);
   note_launch();
   return cudaGetLastError();
 }
