@@ -112,14 +112,16 @@ struct bse_ctx {
   float *psi32 = nullptr, *pdep32 = nullptr, *vloc32 = nullptr, *upsi32 = nullptr;
   // pairs / tau
   int *nbr_ptr = nullptr, *nbr_w = nullptr, *nbr_p = nullptr, *pv = nullptr, *pw = nullptr;
-  // row blocks of four orbitals: union of the rows' neighbours, pair index or -1 per row
+  // row blocks of four orbitals: union of the rows' neighbours (one entry each)
   int *bptr = nullptr, *bw = nullptr;
-  int4* bp = nullptr;
+  int2* tslot = nullptr;     // per pair: the entry slots (4 e + row) that hold its tau
   int n_rblocks = 0;
+  int64_t n_ent = 0;
+  bool tau_entry = false;    // tau stored entry-major for the tiled K1d kernel
   int k1d_sc = 0;            // K1d tile variant chosen by the autotuner (0: not tuned yet)
   bool autotune = true;
   int64_t n_pairs = 0, nnz = 0;
-  void* tau = nullptr;
+  void* tau = nullptr;       // entry-major (tau_entry) or per pair, point-tiled
   // operator workspace
   void *ws_a = nullptr, *ws_r = nullptr, *ws_h = nullptr, *ws_c = nullptr;
   long ws_vecs = 0;
@@ -378,7 +380,7 @@ int autotune_k1d(bse_ctx* c, int nv, long n3, const T* ga, const T* gh, T* gr, d
     float t = 0;
     for (int rep = 0; rep < 2; ++rep) {
       CK(cudaEventRecord(e0, c->st));
-      CK(k1d_tiled<T>(nv, c->n_occ, n3, ga, (const T*)c->tau, c->n_pairs, c->bptr, c->bw, c->bp, c->n_rblocks,
+      CK(k1d_tiled<T>(nv, c->n_occ, n3, ga, (const T*)c->tau, c->n_ent, c->bptr, c->bw, c->n_rblocks,
                       vloc_of<T>(c), gh, upsi_of<T>(c), sf, gr, sc, c->st, n_pts));
       CK(cudaEventRecord(e1, c->st));
       CK(cudaEventSynchronize(e1));
@@ -441,9 +443,9 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
       Scope sc(c, "k1d_combine",
                ((double)c->n_pairs + 2.0 * nf + 1.0 + nv + c->n_occ) * n3 * sz,
                (2.0 * nnz * nv + 5.0 * nf) * n3);
-      if (k1d_default_variant<T>(c->n_occ) > 0 && n3 % 16 == 0) {
+      if (c->tau_entry) {
         if (c->k1d_sc == 0) CA(autotune_k1d<T>(c, (int)nv, n3, (const T*)ga, (const T*)gh, (T*)gr, sf));
-        CK(k1d_tiled<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->n_pairs, c->bptr, c->bw, c->bp,
+        CK(k1d_tiled<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->n_ent, c->bptr, c->bw,
                         c->n_rblocks, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr,
                         c->k1d_sc, c->st));
       } else {
@@ -529,18 +531,32 @@ int build_tau_impl(bse_ctx* c) {
     hbptr.push_back((int)hbw.size());
   }
   c->n_rblocks = nrb;
+  c->n_ent = (int64_t)hbw.size();
+  // entry slots of every pair: (v, w) sits in row v % 4 of entry (block of v, w) and, for
+  // v != w, in row w % 4 of entry (block of w, v)
+  std::vector<int2> hslot(c->n_pairs, make_int2(-1, -1));
+  for (int b = 0; b < nrb; ++b)
+    for (int e = hbptr[b]; e < hbptr[b + 1]; ++e) {
+      const int* qq = &hbp[e].x;
+      for (int i = 0; i < 4; ++i) {
+        const int p = qq[i];
+        if (p < 0) continue;
+        if (hslot[p].x < 0) hslot[p].x = 4 * e + i;
+        else hslot[p].y = 4 * e + i;
+      }
+    }
   dfree(c, c->nbr_ptr); dfree(c, c->nbr_w); dfree(c, c->nbr_p); dfree(c, c->pv); dfree(c, c->pw);
   dfree(c, c->tau); c->tau = nullptr;
   CA(dalloc(c, &c->nbr_ptr, ptr.size()));
   CA(dalloc(c, &c->nbr_w, nw.size()));
   CA(dalloc(c, &c->nbr_p, np.size()));
-  dfree(c, c->bptr); dfree(c, c->bw); dfree(c, c->bp);
+  dfree(c, c->bptr); dfree(c, c->bw); dfree(c, c->tslot);
   CA(dalloc(c, &c->bptr, hbptr.size()));
-  CA(dalloc(c, &c->bw, hbw.size()));
-  CA(dalloc(c, &c->bp, hbp.size()));
+  CA(dalloc(c, &c->bw, std::max<size_t>(1, hbw.size())));
+  CA(dalloc(c, &c->tslot, hslot.size()));
   CK(cudaMemcpyAsync(c->bptr, hbptr.data(), sizeof(int) * hbptr.size(), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->bw, hbw.data(), sizeof(int) * hbw.size(), cudaMemcpyHostToDevice, c->st));
-  CK(cudaMemcpyAsync(c->bp, hbp.data(), sizeof(int4) * hbp.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->tslot, hslot.data(), sizeof(int2) * hslot.size(), cudaMemcpyHostToDevice, c->st));
   CA(dalloc(c, &c->pv, c->pv_h.size()));
   CA(dalloc(c, &c->pw, c->pw_h.size()));
   CK(cudaMemcpyAsync(c->nbr_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, c->st));
@@ -549,8 +565,16 @@ int build_tau_impl(bse_ctx* c) {
   CK(cudaMemcpyAsync(c->pv, c->pv_h.data(), sizeof(int) * c->pv_h.size(), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->pw, c->pw_h.data(), sizeof(int) * c->pw_h.size(), cudaMemcpyHostToDevice, c->st));
   // tau_vw = v^{1/2} (1 + chi_bar) v^{1/2} (psi_v psi_w), batched over pairs
+  // the tiled K1d kernel reads tau entry-major (four rows per entry, zeros where a row lacks
+  // the neighbour); the untiled fallback reads it per pair
   T* tau;
-  CA(dalloc(c, &tau, (size_t)c->n_pairs * n3));
+  c->tau_entry = k1d_default_variant<T>(c->n_occ) > 0 && n3 % TAU_TB == 0;
+  if (c->tau_entry) {
+    CA(dalloc(c, &tau, (size_t)c->n_ent * 4 * n3));
+    CK(cudaMemsetAsync(tau, 0, sizeof(T) * (size_t)c->n_ent * 4 * n3, c->st));
+  } else {
+    CA(dalloc(c, &tau, (size_t)c->n_pairs * n3));
+  }
   c->tau = tau;
   const size_t budget = (size_t)2 << 30;
   long nb = (long)(budget / (n3 * sizeof(cplx<T>))) * 2;
@@ -595,7 +619,8 @@ int build_tau_impl(bse_ctx* c) {
     }
     CK(grid_coulomb<T>(grids, ng, c->N, c->L, c->omega, 1, 1.0, c->st));
     CK(fft3d<T>(grids, ng, c->N, +1, tw_of<T>(c), c->st));
-    CK(deinterleave_pairs<T>(b, grids, n3, p0, c->n_pairs, tau, c->st));
+    if (c->tau_entry) CK(scatter_tau4<T>(b, grids, n3, p0, c->tslot, c->n_ent, tau, c->st));
+    else CK(deinterleave_pairs<T>(b, grids, n3, p0, c->n_pairs, tau, c->st));
   }
   CK(cudaStreamSynchronize(c->st));
   dfree(c, grids); dfree(c, X); dfree(c, X2); dfree(c, Cp);
@@ -1592,8 +1617,8 @@ int apply_static_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out, unsigned 
     CK(fft3d<T>(gh, nh, N, +1, tw_of<T>(c), c->st));
   }
   if (nf & 1) CK(cudaMemsetAsync(gr + (ngr - 1) * n3, 0, (size_t)n3 * sizeof(cplx<T>), c->st));
-  if (k1d_default_variant<T>(c->n_occ) > 0 && n3 % 16 == 0) {
-    CK(k1d_tiled<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, c->n_pairs, c->bptr, c->bw, c->bp,
+  if (c->tau_entry) {
+    CK(k1d_tiled<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, c->n_ent, c->bptr, c->bw,
                     c->n_rblocks, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->k1d_sc,
                     c->st));
   } else {

@@ -49,6 +49,16 @@ __host__ __device__ __forceinline__ size_t tau_off(long p, long r, long n_pairs)
   return ((size_t)(r / TAU_TB) * (size_t)n_pairs + (size_t)p) * TAU_TB + (size_t)(r % TAU_TB);
 }
 
+// Entry-major tau of the tiled K1d kernel. The row-block lists hold, for every block of
+// four orbital rows, the union of the rows' neighbours w (one "entry" each); entry e keeps
+// the four rows' tau_{v_i w}(r) side by side, point-tiled like tau:
+// [n3/TAU_TB][n_ent][TAU_TB][4], zero where a row does not have that neighbour. A lane
+// reads an entry's four values at its point as one 16-byte load (two for FP64), and the
+// lanes of eight consecutive points read 128 contiguous bytes.
+__host__ __device__ __forceinline__ size_t tau4_off(long e, long r, long n_ent) {
+  return (((size_t)(r / TAU_TB) * (size_t)n_ent + (size_t)e) * TAU_TB + (size_t)(r % TAU_TB)) * 4;
+}
+
 namespace bse {
 // count of kernel launches issued by this library (host side, all contexts)
 void note_launch();

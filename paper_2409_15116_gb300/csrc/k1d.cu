@@ -12,11 +12,13 @@
 //    (no registers held, all copies in flight at once), laid out [w][t][s] so that a lane
 //    reads the SC values it needs for orbital w as one or two 16-byte loads;
 //  * groups of TR lanes (one lane per point; TR = 8, 16 or 32) walk row blocks of four orbitals (one
-//    localisation site); each block lists the union of its rows' neighbours w, with the
-//    four pair indices (-1 where a row has no such neighbour, Eq. overlap);
+//    localisation site); each block lists the union of its rows' neighbours w (Eq. overlap);
+//  * tau is stored entry-major: the four rows' values of one block entry at one point are
+//    adjacent, so a lane fetches them with one 16-byte load (zeros stand in for rows
+//    without that neighbour) and only the neighbour index w is broadcast in the group;
 //  * tau values go straight from global memory to registers through a ring of PD entries,
 //    so PD entries of loads are in flight per lane while the oldest one is consumed; tau is
-//    stored point-tiled, so the tau a CTA reads is one contiguous stretch of memory;
+//    point-tiled, so the tau a CTA reads is one contiguous stretch of memory;
 //  * each tau value feeds SC multiply-adds and each staged a value four, accumulated in
 //    packed FP32x2 FMAs for single precision.
 #include "common.cuh"
@@ -124,12 +126,24 @@ struct RowAcc<float, SC, true> {
 template <int TR>
 __device__ __forceinline__ int gshfl(unsigned mask, int v, int j) { return __shfl_sync(mask, v, j, TR); }
 
+// the four rows' tau of one entry at one point (16 bytes per 16-byte load)
+template <typename T>
+__device__ __forceinline__ void ld_tau4(T (&tv)[4], const T* p) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    tv[0] = q.x; tv[1] = q.y; tv[2] = q.z; tv[3] = q.w;
+  } else {
+    const double2 q0 = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 q1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    tv[0] = q0.x; tv[1] = q0.y; tv[2] = q1.x; tv[3] = q1.y;
+  }
+}
+
 template <typename T, int TR, int SC, int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) k1d_tile_kernel(
-    int n_vec, int n_occ, long n3, const T* __restrict__ a, const T* __restrict__ tau, long n_pairs,
-    const int* __restrict__ bptr, const int* __restrict__ bw, const int4* __restrict__ bp,
-    int n_blocks, const T* __restrict__ vloc, const T* __restrict__ vh,
-    const T* __restrict__ upsi, T sf, T* __restrict__ out) {
+    int n_vec, int n_occ, long n3, const T* __restrict__ a, const T* __restrict__ tau4, long n_ent,
+    const int* __restrict__ bptr, const int* __restrict__ bw, int n_blocks, const T* __restrict__ vloc,
+    const T* __restrict__ vh, const T* __restrict__ upsi, T sf, T* __restrict__ out) {
   // ring depth (divides TR); half as deep in double precision, whose values take two registers
   constexpr int PD0 = (sizeof(T) == 8) ? K1D_PD / 2 : K1D_PD;
   constexpr int PD = (PD0 < TR) ? PD0 : TR;
@@ -162,41 +176,34 @@ __global__ void __launch_bounds__(NT, 512 / NT) k1d_tile_kernel(
   cp_async_wait_all();
   __syncthreads();
   const T vl = vloc[r];
-  const T* tau_r = tau + tau_off(0, r, n_pairs);     // pair p at tau_r[p * TAU_TB]
+  const T* tau_r = tau4 + tau4_off(0, r, n_ent);     // entry e at tau_r[e * 4 TAU_TB]
   const unsigned gmask = (TR == 32) ? 0xffffffffu : (((1u << TR) - 1u) << ((tid & 31) & ~(TR - 1)));
   for (int rb = g; rb < n_blocks; rb += G) {
     RowAcc<T, SC> acc;
     acc.zero();
     const int e0 = bptr[rb], e1 = bptr[rb + 1];
-    // block-entry indices in batches of TR: lane t of the group holds entry base + t.
-    // Three batches are live (current, next, the one after), so an index load has more
-    // than a batch of work to arrive before its tau loads are issued.
-    auto ld_idx = [&](int base, int4& p, int& w) {
-      const int e = base + t;
-      if (e < e1) { p = bp[e]; w = bw[e]; } else { p = make_int4(-1, -1, -1, -1); w = 0; }
-    };
-    int4 pA, pB, pC;
-    int wA, wB, wC;
-    ld_idx(e0, pA, wA);
-    ld_idx(e0 + TR, pB, wB);
+    // neighbour indices in batches of TR: lane t of the group holds entry base + t. Three
+    // batches are live (current, next, the one after), so an index load has more than a
+    // batch of work to arrive before it is needed.
+    auto ld_w = [&](int base) { const int e = base + t; return (e < e1) ? bw[e] : 0; };
+    int wA = ld_w(e0), wB = ld_w(e0 + TR), wC;
     // ring of PD entries in flight: slot d holds tau (four rows) and the neighbour w
     T tq[PD][4];
     int wq[PD];
-    auto issue = [&](int px, int py, int pz, int pw, T (&tv)[4]) {
-      tv[0] = (px >= 0) ? tau_r[(size_t)px * TAU_TB] : (T)0;
-      tv[1] = (py >= 0) ? tau_r[(size_t)py * TAU_TB] : (T)0;
-      tv[2] = (pz >= 0) ? tau_r[(size_t)pz * TAU_TB] : (T)0;
-      tv[3] = (pw >= 0) ? tau_r[(size_t)pw * TAU_TB] : (T)0;
+    auto issue = [&](int e, T (&tv)[4]) {
+      if (e < e1) {
+        ld_tau4<T>(tv, tau_r + (size_t)e * (4 * TAU_TB));
+      } else {
+        tv[0] = tv[1] = tv[2] = tv[3] = (T)0;
+      }
     };
 #pragma unroll
     for (int d = 0; d < PD; ++d) {
-      const int px = gshfl<TR>(gmask, pA.x, d), py = gshfl<TR>(gmask, pA.y, d);
-      const int pz = gshfl<TR>(gmask, pA.z, d), pw = gshfl<TR>(gmask, pA.w, d);
       wq[d] = gshfl<TR>(gmask, wA, d);
-      issue(px, py, pz, pw, tq[d]);
+      issue(e0 + d, tq[d]);
     }
     for (int base = e0; base < e1; base += TR) {
-      ld_idx(base + 2 * TR, pC, wC);
+      wC = ld_w(base + 2 * TR);
 #pragma unroll
       for (int d = 0; d < TR; ++d) {
         if (base + d >= e1) break;
@@ -206,21 +213,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) k1d_tile_kernel(
         acc.mac(tq[sl], av);
         // refill the slot with entry base + d + PD (index from batch A or B)
         const int j = d + PD;
-        int px, py, pz, pw, w;
-        if (j < TR) {
-          px = gshfl<TR>(gmask, pA.x, j); py = gshfl<TR>(gmask, pA.y, j);
-          pz = gshfl<TR>(gmask, pA.z, j); pw = gshfl<TR>(gmask, pA.w, j);
-          w = gshfl<TR>(gmask, wA, j);
-        } else {
-          px = gshfl<TR>(gmask, pB.x, j - TR); py = gshfl<TR>(gmask, pB.y, j - TR);
-          pz = gshfl<TR>(gmask, pB.z, j - TR); pw = gshfl<TR>(gmask, pB.w, j - TR);
-          w = gshfl<TR>(gmask, wB, j - TR);
-        }
-        wq[sl] = w;
-        issue(px, py, pz, pw, tq[sl]);
+        wq[sl] = (j < TR) ? gshfl<TR>(gmask, wA, j) : gshfl<TR>(gmask, wB, j - TR);
+        issue(base + j, tq[sl]);
       }
-      pA = pB; wA = wB;
-      pB = pC; wB = wC;
+      wA = wB;
+      wB = wC;
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -254,8 +251,8 @@ size_t variant_smem(int n_occ, int v) {
 }
 
 template <typename T, int TR, int SC, int NT>
-cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T* tau, long n_pairs, const int* bptr,
-                       const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
+cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T* tau4, long n_ent, const int* bptr,
+                       const int* bw, int n_blocks, const T* vloc, const T* vh,
                        const T* upsi, double sf, T* out, long n_pts, cudaStream_t st) {
   static_assert(NT % TR == 0 && 32 % TR == 0 && NT / TR >= SC, "tile shape");
   if constexpr (sizeof(T) == 8 && SC == 8) {
@@ -271,7 +268,7 @@ cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T* tau, 
     if (e0 != cudaSuccess) return e0;
     const long blocks = (n_pts / TR) * ((n_vec + SC - 1) / SC);
     k1d_tile_kernel<T, TR, SC, NT><<<(unsigned)blocks, NT, smem, st>>>(
-        n_vec, n_occ, n3, a, tau, n_pairs, bptr, bw, bp, n_blocks, vloc, vh, upsi, (T)sf, out);
+        n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi, (T)sf, out);
     note_launch();
     return cudaGetLastError();
   }
@@ -301,8 +298,8 @@ int k1d_default_variant(int n_occ) {
 }
 
 template <typename T>
-cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, long n_pairs, const int* bptr,
-                      const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
+cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau4, long n_ent, const int* bptr,
+                      const int* bw, int n_blocks, const T* vloc, const T* vh,
                       const T* upsi, double sf, T* out, int variant, cudaStream_t st, long n_pts) {
   if (n_vec <= 0) return cudaSuccess;
   if (n_pts < 0) n_pts = n3;
@@ -312,7 +309,7 @@ cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, l
   if (n3 % TAU_TB || TAU_TB % kVariants[variant].tr) return cudaErrorInvalidValue;
 #define BSE_K1D_CASE(V, TR, SC, NT)                                                                  \
   case V:                                                                                            \
-    return launch_k1d<T, TR, SC, NT>(n_vec, n_occ, n3, a, tau, n_pairs, bptr, bw, bp, n_blocks, vloc, vh, upsi, sf, \
+    return launch_k1d<T, TR, SC, NT>(n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi, sf, \
                                  out, n_pts, st);
   switch (variant) {
     BSE_K1D_CASE(1, 16, 8, 512)
@@ -331,8 +328,8 @@ cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, l
 #undef BSE_K1D_CASE
 }
 
-template cudaError_t k1d_tiled<float>(int, int, long, const float*, const float*, long, const int*, const int*, const int4*, int, const float*, const float*, const float*, double, float*, int, cudaStream_t, long);
-template cudaError_t k1d_tiled<double>(int, int, long, const double*, const double*, long, const int*, const int*, const int4*, int, const double*, const double*, const double*, double, double*, int, cudaStream_t, long);
+template cudaError_t k1d_tiled<float>(int, int, long, const float*, const float*, long, const int*, const int*, int, const float*, const float*, const float*, double, float*, int, cudaStream_t, long);
+template cudaError_t k1d_tiled<double>(int, int, long, const double*, const double*, long, const int*, const int*, int, const double*, const double*, const double*, double, double*, int, cudaStream_t, long);
 template bool k1d_fits<float>(int, int);
 template bool k1d_fits<double>(int, int);
 template int k1d_default_variant<float>(int);

@@ -63,6 +63,9 @@ template <typename T>
 cudaError_t pair_product(int nb, const int* pv, const int* pw, const T* upsi, long n3, double scale,
                          cplx<T>* grids, cudaStream_t st);
 template <typename T>
+cudaError_t scatter_tau4(int nb, const cplx<T>* grids, long n3, long p0, const int2* slot, long n_ent, T* tau4,
+                         cudaStream_t st);
+template <typename T>
 cudaError_t deinterleave_pairs(int nb, const cplx<T>* grids, long n3, long p0, long n_pairs, T* tau,
                                cudaStream_t st);
 cudaError_t square_fields(int n, const double* u, long n3, double* rho, cudaStream_t st);
@@ -124,8 +127,8 @@ int k1d_default_variant(int n_occ);
 template <typename T>
 bool k1d_fits(int n_occ, int variant);
 template <typename T>
-cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau, long n_pairs, const int* bptr,
-                      const int* bw, const int4* bp, int n_blocks, const T* vloc, const T* vh,
+cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau4, long n_ent, const int* bptr,
+                      const int* bw, int n_blocks, const T* vloc, const T* vh,
                       const T* upsi, double sf, T* out, int variant, cudaStream_t st, long n_pts = -1);
 template <typename T>
 cudaError_t scale_columns(int rows, int cols, T* C, long ldc, const double* f, cudaStream_t st);

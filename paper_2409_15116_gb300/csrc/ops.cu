@@ -62,6 +62,36 @@ cudaError_t deinterleave_pairs(int nb, const cplx<T>* grids, long n3, long p0, l
   return cudaGetLastError();
 }
 
+// pair values of the batch into the entry-major tau: pair p = (v, w) goes to slot v % 4 of
+// entry (block of v, w) and, for v != w, to slot w % 4 of entry (block of w, v);
+// slot[p] = (4 e1 + i1, 4 e2 + i2 or -1)
+template <typename T>
+__global__ void scatter_tau4_kernel(int nb, const cplx<T>* __restrict__ grids, long n3, long p0,
+                                    const int2* __restrict__ slot, long n_ent, T* __restrict__ tau4) {
+  const long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long c = blockIdx.y;
+  if (r >= n3) return;
+  const cplx<T> F = grids[c * n3 + r];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (2 * c + q >= nb) break;
+    const T val = q ? F.y : F.x;
+    const int2 s = slot[p0 + 2 * c + q];
+    tau4[tau4_off(s.x >> 2, r, n_ent) + (s.x & 3)] = val;
+    if (s.y >= 0) tau4[tau4_off(s.y >> 2, r, n_ent) + (s.y & 3)] = val;
+  }
+}
+
+template <typename T>
+cudaError_t scatter_tau4(int nb, const cplx<T>* grids, long n3, long p0, const int2* slot, long n_ent, T* tau4,
+                         cudaStream_t st) {
+  if (nb <= 0) return cudaSuccess;
+  if (n3 % TAU_TB) return cudaErrorInvalidValue;
+  dim3 grid(nblk(n3), (nb + 1) / 2);
+  scatter_tau4_kernel<T><<<grid, 256, 0, st>>>(nb, grids, n3, p0, slot, n_ent, tau4); note_launch();
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------------
 // overlap (Eq. overlap): |psi_v|^2 on the grid, Gram by GEMM, then normalisation
 // ---------------------------------------------------------------------------------
@@ -507,6 +537,7 @@ bool finite_check_host(const double* x, long n) {
   template cudaError_t pair_product<T>(int, const int*, const int*, const T*, long, double,        \
                                        cplx<T>*, cudaStream_t);                                    \
   template cudaError_t deinterleave_pairs<T>(int, const cplx<T>*, long, long, long, T*, cudaStream_t);       \
+  template cudaError_t scatter_tau4<T>(int, const cplx<T>*, long, long, const int2*, long, T*, cudaStream_t); \
   template cudaError_t hartree_density<T>(int, int, long, const T*, const T*, T*, cudaStream_t);   \
   template cudaError_t k1d_combine<T>(int, int, long, const T*, const T*, long, const int*, const int*,   \
                                       const int*, const T*, const T*, const T*, double, T*,        \
