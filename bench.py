@@ -351,12 +351,20 @@ def main():
     t_launch = d["ms"] / nl * 1e-3
     bytes_launch = d["bytes"] / d["calls"] if name not in per_kernel_launches else d["bytes"] / d["calls"]
     achieved = bytes_launch / t_launch / 1e9
-    # DRAM traffic per launch: the K1d kernel was captured with ncu on the op256 case
-    # (32 vectors, 32^3 grid, 4,934 pairs): 2.800 GB read + written against 2.832 GB of
-    # algorithmic bytes; its traffic scales with the same per-point, per-pair and per-vector
-    # counts, so the ratio carries over to this launch's algorithmic bytes
-    K1D_DRAM_PER_ALGORITHMIC_BYTE = 2.800075 / 2.832204
-    traffic = bytes_launch * K1D_DRAM_PER_ALGORITHMIC_BYTE if name == "k1d_combine" else None
+    # DRAM traffic per launch of the K1d kernel: its entry-major tau (four slots per entry of
+    # the row-block neighbour lists) once, a(r) and the result once, V_loc, V_H and u_psi.
+    # The ncu capture of the op256 launch (32 vectors, 32^3 grid) read and wrote 4.311 GB
+    # where this model gives 4.331 GB; the algorithmic bytes count tau once per pair.
+    traffic = None
+    if name == "k1d_combine":
+        pr = ctx.pairs()
+        n = inst.n_occ
+        nbr = np.zeros((n, n), bool)
+        nbr[pr[:, 0], pr[:, 1]] = True
+        nbr[pr[:, 1], pr[:, 0]] = True
+        n_ent = int(sum(np.any(nbr[b:b + 4], axis=0).sum() for b in range(0, n, 4)))
+        n3 = inst.n_grid ** 3
+        traffic = bytes_launch + (4.0 * n_ent - len(pr)) * n3 * 4.0
     roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "traffic": traffic,
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
