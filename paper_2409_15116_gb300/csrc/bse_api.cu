@@ -480,17 +480,21 @@ int build_tau_impl(bse_ctx* c) {
   const int n = c->n_occ;
   // O_vw in FP64 always, so that the lists do not depend on the precision mode
   {
-    double *rho, *gram, *dg;
-    CA(dalloc(c, &rho, (size_t)n * n3));
+    // the Gram of the densities |psi_v|^2 (FP64 values, split into FP32 hi / lo) in
+    // float-float arithmetic
+    float *rho_hi, *rho_lo;
+    double *gram, *dg;
+    CA(dalloc(c, &rho_hi, (size_t)n * n3));
+    CA(dalloc(c, &rho_lo, (size_t)n * n3));
     CA(dalloc(c, &gram, (size_t)n * n));
     CA(dalloc(c, &dg, (size_t)n));
-    CK(square_fields(n, c->upsi64, n3, rho, c->st));
-    CK((gram_sym<double, double>(n, (int)n3, 1.0, rho, n3, gram, n, c->st)));
+    CK(square_fields_split(n, c->upsi64, n3, rho_hi, rho_lo, c->st));
+    CK(gram_ff(n, n3, rho_hi, rho_lo, n3, gram, n, c->st));
     CK(normalize_overlap(n, gram, dg, c->st));
     c->O_h.assign((size_t)n * n, 0.0);
     CK(cudaMemcpyAsync(c->O_h.data(), gram, sizeof(double) * n * n, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
-    dfree(c, rho); dfree(c, gram); dfree(c, dg);
+    dfree(c, rho_hi); dfree(c, rho_lo); dfree(c, gram); dfree(c, dg);
   }
   if (!all_finite(c->O_h.data(), (long)n * n)) return fail(c, BSE_ERR_NUMERIC, "non-finite overlap");
   c->thr = choose_threshold(c->O_h, n, c->thr_in, c->keep_pairs);

@@ -52,6 +52,10 @@ cudaError_t grid_to_sphere(cplx<T>* grids, long n_fields, int n_pw, int n_half, 
 
 // ---- gemm.cu ----
 // C = alpha A A^T, A n x K row-major: upper-triangle tiles, then mirrored
+// symmetric Gram A A^T of FP64 data given as FP32 hi / lo splits, in float-float arithmetic
+// (about 1e-14 relative)
+cudaError_t gram_ff(int n, long K, const float* Ahi, const float* Alo, long lda, double* C, long ldc,
+                    cudaStream_t st);
 template <typename T, typename TC>
 cudaError_t gram_sym(int n, int K, double alpha, const T* A, long lda, TC* C, long ldc, cudaStream_t st);
 template <typename T, typename TC>
@@ -68,7 +72,7 @@ cudaError_t scatter_tau4(int nb, const cplx<T>* grids, long n3, long p0, const i
 template <typename T>
 cudaError_t deinterleave_pairs(int nb, const cplx<T>* grids, long n3, long p0, long n_pairs, T* tau,
                                cudaStream_t st);
-cudaError_t square_fields(int n, const double* u, long n3, double* rho, cudaStream_t st);
+cudaError_t square_fields_split(int n, const double* u, long n3, float* rho_hi, float* rho_lo, cudaStream_t st);
 cudaError_t normalize_overlap(int n, double* gram, double* diag, cudaStream_t st);
 template <typename T>
 cudaError_t hartree_density(int n_vec, int n_occ, long n3, const T* a, const T* upsi, T* h,

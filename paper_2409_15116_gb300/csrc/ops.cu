@@ -95,18 +95,22 @@ cudaError_t scatter_tau4(int nb, const cplx<T>* grids, long n3, long p0, const i
 // ---------------------------------------------------------------------------------
 // overlap (Eq. overlap): |psi_v|^2 on the grid, Gram by GEMM, then normalisation
 // ---------------------------------------------------------------------------------
-__global__ void square_fields_kernel(int n, const double* __restrict__ u, long n3,
-                                     double* __restrict__ rho) {
+// |psi_v(r)|^2 in FP64, stored as the FP32 split hi = fp32(x), lo = fp32(x - hi)
+__global__ void square_fields_split_kernel(int n, const double* __restrict__ u, long n3,
+                                           float* __restrict__ hi, float* __restrict__ lo) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long)n * n3) return;
   const long v = idx / n3, r = idx - v * n3;
   const double x = u[pair_off<double>(v, r, n3)];
-  rho[idx] = x * x;
+  const double rho = x * x;
+  const float h = (float)rho;
+  hi[idx] = h;
+  lo[idx] = (float)(rho - (double)h);
 }
-cudaError_t square_fields(int n, const double* u, long n3, double* rho, cudaStream_t st) {
+cudaError_t square_fields_split(int n, const double* u, long n3, float* rho_hi, float* rho_lo, cudaStream_t st) {
   const long tot = (long)n * n3;
   if (!tot) return cudaSuccess;
-  square_fields_kernel<<<nblk(tot), 256, 0, st>>>(n, u, n3, rho); note_launch();
+  square_fields_split_kernel<<<nblk(tot), 256, 0, st>>>(n, u, n3, rho_hi, rho_lo); note_launch();
   return cudaGetLastError();
 }
 
