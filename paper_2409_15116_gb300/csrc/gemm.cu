@@ -182,8 +182,8 @@ static cudaError_t dispatch_t(bool at, bool bt, int M, int N, int K, double alph
 //         with double-precision atomics.
 // ts_nn:  C (M x N) = alpha op(A) B + beta C with op(A) M x K small (K <= 256) and N in the
 //         millions (CGS update, Cholesky-QR, Ritz vectors, restart). op(A) sits in shared
-//         memory; a thread owns four adjacent columns and a band of up to 16 rows,
-//         streaming B straight from global memory in 16-byte loads.
+//         memory; a thread owns four adjacent columns and a band of up to 16 rows, and
+//         streams its 16-byte pieces of B through a private cp.async ring twelve rows deep.
 // ---------------------------------------------------------------------------------
 namespace {
 
@@ -341,6 +341,8 @@ __global__ void __launch_bounds__(256, 2) ts_tn_kernel(int M, int N, long K, lon
   }
 }
 
+constexpr int NN_PD = 12;      // B rows in flight per thread (ts_nn)
+
 template <int MT, bool AT>
 __global__ void __launch_bounds__(256) ts_gemm_nn_kernel(int M, long N, int K, double alpha,
                                                         const float* __restrict__ A, long lda,
@@ -348,52 +350,51 @@ __global__ void __launch_bounds__(256) ts_gemm_nn_kernel(int M, long N, int K, d
                                                         double beta, float* __restrict__ C, long ldc) {
   extern __shared__ __align__(16) float ts_smem[];
   float* S = ts_smem;                                // [K][MT]: op(A)[i0 + i][k]
+  // per-thread ring of NN_PD rows of B (16 bytes each), filled by cp.async: the loads in
+  // flight take no registers, so each thread keeps NN_PD of them outstanding
+  float4* ring = reinterpret_cast<float4*>(ts_smem + ((K * MT + 3) / 4) * 4);   // [NN_PD][256]
   const int i0 = blockIdx.x * MT;                    // row band (fastest: bands share B in L2)
   for (int e = threadIdx.x; e < K * MT; e += 256) {
     const int k = e / MT, i = e - k * MT;
     const int gi = i0 + i;
     S[e] = (gi < M) ? (AT ? A[(long)k * lda + gi] : A[(long)gi * lda + k]) : 0.f;
   }
-  __syncthreads();
   const long d = 4 * ((long)blockIdx.y * 256 + threadIdx.x);
-  if (d >= N) return;
+  const bool act = d < N;
+  const float* bp = B + (act ? d : 0);
+  auto fetch = [&](int k) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(ring + (k % NN_PD) * 256 + threadIdx.x);
+    const int nb = (act && k < K) ? 16 : 0;        // 0: zero-fill, read nothing
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n"
+                 ::"r"(sa), "l"(bp + (long)(k < K ? k : 0) * ldb), "r"(nb) : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+#pragma unroll
+  for (int k = 0; k < NN_PD - 1; ++k) fetch(k);
+  __syncthreads();
   float2 acc[MT][2];
 #pragma unroll
   for (int i = 0; i < MT; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
-  const float* bp = B + d;
-  int k = 0;
-  for (; k + 4 <= K; k += 4) {
-    float4 v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const float4*>(bp + (long)(k + u) * ldb);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const float* sk = S + (k + u) * MT;
-      const float2 v0 = make_float2(v[u].x, v[u].y), v1 = make_float2(v[u].z, v[u].w);
-#pragma unroll
-      for (int i = 0; i < MT; i += 4) {
-        const float4 s4 = *reinterpret_cast<const float4*>(sk + i);
-        const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float2 sq = make_float2(sv[q], sv[q]);
-          acc[i + q][0] = __ffma2_rn(sq, v0, acc[i + q][0]);
-          acc[i + q][1] = __ffma2_rn(sq, v1, acc[i + q][1]);
-        }
-      }
-    }
-  }
-  for (; k < K; ++k) {
-    const float4 v = *reinterpret_cast<const float4*>(bp + (long)k * ldb);
+  for (int k = 0; k < K; ++k) {
+    fetch(k + NN_PD - 1);
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NN_PD - 1) : "memory");
+    const float4 v = ring[(k % NN_PD) * 256 + threadIdx.x];
     const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
     const float* sk = S + k * MT;
 #pragma unroll
-    for (int i = 0; i < MT; ++i) {
-      const float2 sq = make_float2(sk[i], sk[i]);
-      acc[i][0] = __ffma2_rn(sq, v0, acc[i][0]);
-      acc[i][1] = __ffma2_rn(sq, v1, acc[i][1]);
+    for (int i = 0; i < MT; i += 4) {
+      const float4 s4 = *reinterpret_cast<const float4*>(sk + i);
+      const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 sq = make_float2(sv[q], sv[q]);
+        acc[i + q][0] = __ffma2_rn(sq, v0, acc[i + q][0]);
+        acc[i + q][1] = __ffma2_rn(sq, v1, acc[i + q][1]);
+      }
     }
   }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  if (!act) return;
   const float al = (float)alpha, be = (float)beta;
 #pragma unroll
   for (int i = 0; i < MT; ++i) {
@@ -459,7 +460,17 @@ cudaError_t ts_gemm_tn(int M, int N, long K, double alpha, const float* A, long 
 template <int MT>
 cudaError_t ts_nn_launch(bool at, int M, long N, int K, double alpha, const float* A, long lda,
                          const float* B, long ldb, double beta, float* C, long ldc, cudaStream_t st) {
-  const size_t smem = (size_t)K * MT * sizeof(float);
+  // op(A) for K <= 256 rows plus the B ring: at most 16 KB + 48 KB
+  static std::once_flag once;
+  static cudaError_t once_st = cudaSuccess;
+  cudaError_t e0 = once_status(once, once_st, [&] {
+    const int mx = (int)((256 * MT + 3) / 4 * 16 + (size_t)NN_PD * 256 * 16);
+    cudaError_t e = cudaFuncSetAttribute(ts_gemm_nn_kernel<MT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(ts_gemm_nn_kernel<MT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  });
+  if (e0 != cudaSuccess) return e0;
+  const size_t smem = ((size_t)K * MT + 3) / 4 * 16 + (size_t)NN_PD * 256 * 16;
   dim3 grid((unsigned)((M + MT - 1) / MT), (unsigned)((N / 4 + 255) / 256));
   if (at) ts_gemm_nn_kernel<MT, true><<<grid, 256, smem, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   else ts_gemm_nn_kernel<MT, false><<<grid, 256, smem, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
