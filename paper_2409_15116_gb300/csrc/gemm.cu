@@ -1,8 +1,9 @@
-// Tiled SIMT GEMM, C = alpha * op(A) op(B) + beta * C, with optional split-K.
+// Tiled SIMT GEMM, C = alpha * op(A) op(B) + beta * C, with optional split-K, plus the
+// tall-skinny products of the Davidson algebra and the float-float overlap Gram (below).
 //
-// Used for the conduction projector P_c = 1 - sum_v |psi_v><psi_v| (Section 2), the
-// PDEP projection of Eq. (pdep), the overlap Gram of Eq. (overlap) and the Davidson
-// subspace algebra. op(A) is A (row-major M x K) or A^T (A stored K x M); op(B) is B
+// The tiled GEMM serves the conduction projector P_c = 1 - sum_v |psi_v><psi_v| (Section
+// 2) and the PDEP projection of Eq. (pdep) in the FP64 path, and the Davidson subspace
+// algebra where the tall-skinny kernels do not apply. op(A) is A (row-major M x K) or A^T (A stored K x M); op(B) is B
 // (row-major K x N) or B^T (B stored N x K). With DFLUSH the products accumulate in
 // the input precision over 256-term runs and the runs are summed in double: FP32
 // products with FP64 accumulation for the Davidson Gram and Rayleigh-Ritz matrices.
@@ -11,7 +12,7 @@
 
 namespace bse {
 
-template <typename T, typename TC, bool AT, bool BT, int TM, int TN, bool DFLUSH, bool TRI = false>
+template <typename T, typename TC, bool AT, bool BT, int TM, int TN, bool DFLUSH>
 __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, double alpha,
                                                   const T* __restrict__ A, long lda,
                                                   const T* __restrict__ B, long ldb, double beta,
@@ -21,16 +22,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, double a
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  long ti = blockIdx.y, tj = blockIdx.x;
-  if constexpr (TRI) {
-    // blockIdx.x enumerates the tiles (ti <= tj) of the upper triangle, row by row
-    const int nt = (N + BN - 1) / BN;
-    long r = blockIdx.x;
-    ti = 0;
-    while (r >= nt - ti) { r -= nt - ti; ++ti; }
-    tj = ti + r;
-  }
-  const long i0 = ti * BM, j0 = tj * BN;
+  const long i0 = (long)blockIdx.y * BM, j0 = (long)blockIdx.x * BN;
   const long kbeg = (long)blockIdx.z * k_chunk;
   const long kend = (kbeg + k_chunk < K) ? kbeg + k_chunk : K;
   T acc[TM][TN];
@@ -489,8 +481,8 @@ cudaError_t ts_gemm_nn(bool at, int M, long N, int K, double alpha, const float*
 }  // namespace
 
 // ---------------------------------------------------------------------------------
-// Symmetric Gram C = alpha A A^T (A n x K row-major, C n x n): only the tiles on and
-// above the diagonal are computed (split over K with atomics), then mirrored.
+// C[i][j] = C[j][i] for i > j: completes a symmetric result of which only the entries on
+// and above the diagonal were computed
 // ---------------------------------------------------------------------------------
 namespace {
 template <typename TC>
@@ -502,32 +494,6 @@ __global__ void mirror_upper_kernel(int n, TC* C, long ldc) {
 }
 }  // namespace
 
-template <typename T, typename TC>
-cudaError_t gram_sym(int n, int K, double alpha, const T* A, long lda, TC* C, long ldc, cudaStream_t st) {
-  constexpr int TM = 4, BM = 64;
-  if (n <= 0) return cudaSuccess;
-  constexpr bool DF = sizeof(T) < sizeof(TC);
-  const long nt = (n + BM - 1) / BM;
-  const long tiles = nt * (nt + 1) / 2;
-  long s = tiles >= 304 ? 1 : (304 + tiles - 1) / tiles;
-  const long kmax = (K + 255) / 256;
-  if (s > kmax) s = kmax;
-  if (s < 1) s = 1;
-  int k_chunk = (int)((K + s - 1) / s);
-  k_chunk = (k_chunk + 15) / 16 * 16;
-  if (k_chunk <= 0) k_chunk = 16;
-  const int splitk = (int)((K + k_chunk - 1) / k_chunk);
-  const long tot = (long)n * n;
-  scale_matrix_kernel<TC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, n, C, ldc, 0.0); note_launch();
-  if (K > 0) {
-    dim3 grid((unsigned)tiles, 1, (unsigned)(splitk < 1 ? 1 : splitk));
-    gemm_kernel<T, TC, false, true, TM, TM, DF, true><<<grid, 256, 0, st>>>(n, n, K, alpha, A, lda, A, lda, 0.0, C,
-                                                                           ldc, k_chunk, 1); note_launch();
-  }
-  mirror_upper_kernel<TC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, C, ldc); note_launch();
-  return cudaGetLastError();
-}
-template cudaError_t gram_sym<double, double>(int, int, double, const double*, long, double*, long, cudaStream_t);
 
 // ---------------------------------------------------------------------------------
 // Symmetric Gram of FP64 data in float-float arithmetic: C = A A^T (A n x K, FP64, given as

@@ -57,8 +57,6 @@ cudaError_t grid_to_sphere(cplx<T>* grids, long n_fields, int n_pw, int n_half, 
 cudaError_t gram_ff(int n, long K, const float* Ahi, const float* Alo, long lda, double* C, long ldc,
                     cudaStream_t st);
 template <typename T, typename TC>
-cudaError_t gram_sym(int n, int K, double alpha, const T* A, long lda, TC* C, long ldc, cudaStream_t st);
-template <typename T, typename TC>
 cudaError_t gemm(bool at, bool bt, int M, int N, int K, double alpha, const T* A, long lda,
                  const T* B, long ldb, double beta, TC* C, long ldc, int splitk, cudaStream_t st);
 
