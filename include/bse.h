@@ -85,7 +85,8 @@ typedef struct {
  * stream: a cudaStream_t (NULL = legacy default stream). Device = current device. */
 int bse_create(const bse_system* sys, int precision, void* stream, bse_ctx** out);
 
-/* Overlaps O_vw (Eq. overlap, FP64 grid quadrature), the pair rule, and the screened
+/* Overlaps O_vw (Eq. overlap, grid quadrature of FP64 densities, accumulated in float-float
+ * arithmetic to about 1e-14 relative, in both precision modes), the pair rule, and the screened
  * integrals tau_vw = W[psi_v psi_w] for every kept pair v <= w (Eqs. tau,
  * tau_from_tau_u, pdep). Pair rule: keep iff O_vw >= thr; with keep_pairs the
  * threshold is the midpoint of the gap between the k-th and (k+1)-th largest
