@@ -570,9 +570,20 @@ int build_tau_impl(bse_ctx* c) {
   CK(cudaMemcpyAsync(c->pw, c->pw_h.data(), sizeof(int) * c->pw_h.size(), cudaMemcpyHostToDevice, c->st));
   // tau_vw = v^{1/2} (1 + chi_bar) v^{1/2} (psi_v psi_w), batched over pairs
   // the tiled K1d kernel reads tau entry-major (four rows per entry, zeros where a row lacks
-  // the neighbour); the untiled fallback reads it per pair
+  // the neighbour); the untiled fallback reads it per pair. The entry-major layout holds
+  // about 2.8 times the per-pair values, so it is used only while it takes at most half of
+  // the free device memory (large FP64 systems keep the per-pair layout);
+  // BSE_TAU_LAYOUT=pair forces the per-pair layout and the untiled kernel.
   T* tau;
-  c->tau_entry = k1d_default_variant<T>(c->n_occ) > 0 && n3 % TAU_TB == 0;
+  {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    const double t4 = (double)c->n_ent * 4.0 * (double)n3 * sizeof(T);
+    const char* lay = getenv("BSE_TAU_LAYOUT");
+    const bool force_pair = lay && std::strcmp(lay, "pair") == 0;
+    c->tau_entry = !force_pair && k1d_default_variant<T>(c->n_occ) > 0 && n3 % TAU_TB == 0 &&
+                   t4 <= 0.5 * (double)fr;
+  }
   if (c->tau_entry) {
     CA(dalloc(c, &tau, (size_t)c->n_ent * 4 * n3));
     CK(cudaMemsetAsync(tau, 0, sizeof(T) * (size_t)c->n_ent * 4 * n3, c->st));

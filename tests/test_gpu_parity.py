@@ -146,6 +146,20 @@ def ragged_case():
     return inst, A, Lop.apply(A)
 
 
+# the per-pair tau layout with the untiled K1d kernel, which the library uses when the
+# entry-major layout would take more than half of the free device memory
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
+def test_per_pair_tau_untiled_vs_matrix_free(ragged_case, prec, tol, monkeypatch):
+    inst, A, ref = ragged_case
+    monkeypatch.setenv("BSE_TAU_LAYOUT", "pair")
+    c = ctx_for(inst, prec)
+    a = dev(A, prec)
+    out = torch.empty_like(a)
+    c.apply(a, out)
+    got = out.double().cpu().numpy()
+    assert rel(got, ref) <= tol, rel(got, ref)
+
+
 @pytest.mark.parametrize("variant", range(1, 12))
 @pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
 def test_k1d_tile_variants_vs_matrix_free(ragged_case, variant, prec, tol, monkeypatch):
