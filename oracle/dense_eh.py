@@ -25,6 +25,7 @@ import numpy as np
 from .basis import (full_miller, packing_matrix, drop_pad, add_pad, coulomb_grid,
                     sphere_on_grid, packed_to_full)
 from .pairs import pair_mask
+from .qp import qp_terms, occupied_energy_matrix
 
 
 def ks_hamiltonian_packed(inst) -> np.ndarray:
@@ -113,8 +114,12 @@ def eh_hamiltonian(inst, mask=None, with_parts: bool = False):
     c_r = real_space_explicit(inst, Xc)                  # [Nc, N^3]
     vc = coulomb_grid(N, inst.L).reshape(-1)
 
-    # D: diagonal in the conduction eigenbasis (Eq. d with a pure scissor, Eq. ham)
-    Ddiag = (eps_c[None, :] + inst.scissor - inst.eps[:, None]).reshape(-1)
+    # D: P_c H_KS P_c is diagonal in the conduction eigenbasis; the QP Hamiltonian of Eq. ham
+    # adds Delta - eps^QP_v and, with explicit QP data, sum_c psi_c delta_c <psi_c| (Eq. d)
+    eps_qp, delta_avg, delta_c, psi_qp = qp_terms(inst)
+    E = occupied_energy_matrix(inst)
+    Ddiag = (eps_c[None, :] + delta_avg - np.diag(E)[:, None]).reshape(-1)
+    Cqp = (Xc @ psi_qp.T) @ np.diag(delta_c) @ (psi_qp @ Xc.T)     # [Nc, Nc]
 
     # K1e core: Omega sum_G v(G) rho_vc^* rho_wc' (Eq. k1e, without the spin factor)
     rho_hat = _hat((psi_r[:, None, :] * c_r[None, :, :]).reshape(No * Nc, -1), N)
@@ -131,10 +136,11 @@ def eh_hamiltonian(inst, mask=None, with_parts: bool = False):
             K1d[v * Nc:(v + 1) * Nc, w * Nc:(w + 1) * Nc] = dV * (c_r * tau_r) @ c_r.T
 
     s = 2.0 if inst.spin == 0 else 0.0
-    H = np.diag(Ddiag) + s * K1e - K1d
+    H = np.diag(Ddiag) + np.kron(np.eye(No), Cqp) - np.kron(E - np.diag(np.diag(E)), np.eye(Nc)) \
+        + s * K1e - K1d
     if not with_parts:
         return H
-    return H, dict(D=Ddiag, K1e=K1e, K1d=K1d, eps_c=eps_c, Xc=Xc, psi_r=psi_r,
+    return H, dict(D=Ddiag, Dqp=Cqp, K1e=K1e, K1d=K1d, eps_c=eps_c, Xc=Xc, psi_r=psi_r,
                    c_r=c_r, mask=mask, spin_factor=s)
 
 

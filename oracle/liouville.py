@@ -19,7 +19,8 @@ import numpy as np
 
 from .basis import (packed_to_grid_field, grid_field_to_packed, coulomb_grid, full_miller,
                     sphere_on_grid, full_to_packed, packed_to_full, g2_packed)
-from .pairs import pair_mask
+from .pairs import pair_mask, channels
+from .qp import qp_terms, occupied_energy_matrix
 
 
 class Liouville:
@@ -38,7 +39,15 @@ class Liouville:
         iz, iy, ix = sphere_on_grid(full_miller(inst.miller), N)
         self.sidx = (iz, iy, ix)
         self.f = inst.lam / (1.0 - inst.lam)
-        self.spin_factor = 2.0 if inst.spin == 0 else 0.0
+        # K1e factor (Eq. k1e): 2 for a closed-shell singlet, 0 for the triplet; in a
+        # spin-polarised system every orbital is one spin-orbital and the Hartree term of the
+        # total density change enters each channel once
+        self.ch = channels(inst)
+        self.polarised = bool(getattr(inst, "n_up", 0))
+        self.spin_factor = 1.0 if self.polarised else (2.0 if inst.spin == 0 else 0.0)
+        self.eps_qp, self.delta_avg, self.delta_c, self.psi_qp = qp_terms(inst)
+        self.E = occupied_energy_matrix(inst)
+        self.E_off = self.E - np.diag(np.diag(self.E))
         self._tau = {}
 
     # -- screened integrals ------------------------------------------------------
@@ -79,31 +88,53 @@ class Liouville:
 
     def apply(self, A: np.ndarray, rows=None, project: bool = True) -> np.ndarray:
         """R = (D + K1e - K1d) A for A [B, n_occ, n_pw]; only rows v in ``rows`` if given."""
+        A = np.asarray(A, dtype=np.float64)
+        ua, VH = self.fields(A)
+        R = self.apply_rows(A, ua, VH, rows)
+        if project:
+            R = self.project(R)
+        return R
+
+    def fields(self, A: np.ndarray):
+        """The trial orbitals on the grid and their Hartree potentials (per vector, all rows)."""
+        ua = packed_to_grid_field(np.asarray(A, dtype=np.float64), self.inst.miller, self.N)
+        return ua, self.hartree(ua)                          # [B, n_occ, N, N, N], [B, N, N, N]
+
+    def apply_rows(self, A: np.ndarray, ua: np.ndarray, VH: np.ndarray, rows=None) -> np.ndarray:
+        """Rows v of (D + K1e - K1d) A before P_c, given the fields of ``A`` (Eqs. d, k1e, k1d)."""
         inst, N = self.inst, self.N
         A = np.asarray(A, dtype=np.float64)
         B, n_occ, n_pw = A.shape
-        ua = packed_to_grid_field(A, inst.miller, N)        # [B, n_occ, N, N, N]
-        VH = self.hartree(ua)
         rows = range(n_occ) if rows is None else rows
         R = np.zeros_like(A)
         for v in rows:
             uR = self.vloc * ua[:, v] + self.spin_factor * VH * self.u_psi[v]
             for w in np.nonzero(self.mask[v])[0]:
                 uR = uR - self.tau(v, w) * ua[:, w]
-            dmul = 0.5 * self.g2 + inst.scissor - inst.eps[v]
+            dmul = 0.5 * self.g2 + self.delta_avg - self.E[v, v]
             dmul[1] = 0.0                                   # pad coordinate is not a G
             R[:, v] = grid_field_to_packed(uR, inst.miller, N) + dmul * A[:, v]
-        if project:
-            R = self.project(R)
+            if self.E_off[v].any():                         # rotated frame: - sum_w E_vw a_w
+                R[:, v] -= np.einsum("w,bwj->bj", self.E_off[v], A)
+            if self.delta_c.size:                           # explicit QP terms (Eq. ham)
+                R[:, v] += ((A[:, v] @ self.psi_qp.T) * self.delta_c) @ self.psi_qp
         return R
 
     def project(self, R: np.ndarray) -> np.ndarray:
-        """P_c = 1 - sum_u |psi_u><psi_u| applied to every orbital of every vector.
+        """P_c = 1 - sum_u |psi_u><psi_u| applied to every orbital of every vector (the sum over
+        the orbital's own spin channel in a spin-polarised system).
 
         The pad coordinate (packed index 1) is not part of the function space and is zeroed.
         """
         psi = self.inst.psi
-        out = R - (R @ psi.T) @ psi
+        if not self.polarised:
+            out = R - (R @ psi.T) @ psi
+        else:                                               # P_c of each spin channel
+            out = R.copy()
+            for c in (0, 1):
+                sel = self.ch == c
+                if sel.any():
+                    out[..., sel, :] -= (R[..., sel, :] @ psi[sel].T) @ psi[sel]
         out[..., 1] = 0.0
         return out
 
@@ -111,4 +142,4 @@ class Liouville:
         """Preconditioner diagonal 1/2|G|^2 + V(0) + Delta - eps_v, [n_occ, n_pw]."""
         inst = self.inst
         v0 = float(inst.v_loc.mean())
-        return 0.5 * self.g2[None, :] + v0 + inst.scissor - inst.eps[:, None]
+        return 0.5 * self.g2[None, :] + v0 + self.delta_avg - np.diag(self.E)[:, None]

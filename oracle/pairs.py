@@ -56,10 +56,25 @@ def choose_threshold(O: np.ndarray, thr: float, keep_pairs: int) -> float:
     return float(0.5 * (off[j - 1] + off[j]))
 
 
+def channels(inst) -> np.ndarray:
+    """Spin channel of every orbital: 0 up, 1 down (all 0 for a closed shell)."""
+    ch = np.zeros(inst.n_occ, dtype=np.int64)
+    n_up = int(getattr(inst, "n_up", 0) or 0)
+    if n_up:
+        ch[n_up:] = 1
+    return ch
+
+
 def pair_mask(inst, O: np.ndarray | None = None) -> tuple[np.ndarray, float]:
-    """Boolean m_vw (symmetric, diagonal true) and the threshold applied."""
+    """Boolean m_vw (symmetric, diagonal true) and the threshold applied.
+
+    In a spin-polarised system tau_vw couples orbitals of one spin channel only (the screened
+    direct term conserves spin), so pairs across channels are never kept and do not enter the
+    threshold rule (they get the overlap -1, below every real overlap in [0, 1])."""
     if O is None:
         O = overlaps(inst)
+    ch = channels(inst)
+    O = np.where(ch[:, None] == ch[None, :], O, -1.0)
     t = choose_threshold(O, inst.overlap_thr, inst.keep_pairs)
     m = np.triu(O >= t, 1)
     m = m | m.T

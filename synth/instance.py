@@ -53,6 +53,18 @@ class Instance:
     seed: int = 0
     n_eig: int = 4
     block: int = 8
+    # explicit quasi-particle energies (Eq. ham): 0 = scissor only; else N_QP > n_occ with
+    # the conduction KS states n_occ..N_QP-1 (packed), KS and QP energies of states 0..N_QP-1
+    qp_n: int = 0
+    qp_psi: np.ndarray | None = None
+    qp_eps_ks: np.ndarray | None = None
+    qp_eps: np.ndarray | None = None
+    # spin-polarised (spin-conserving) systems: orbitals 0..n_up-1 are spin up, the rest spin
+    # down; 0 = closed shell (the `spin` field then selects singlet or triplet)
+    n_up: int = 0
+    # occupied energies as a matrix in a rotated (e.g. Wannier) frame, U^T diag(eps) U; None:
+    # the orbitals are canonical and eps is diagonal
+    eps_mat: np.ndarray | None = None
 
     @property
     def n_occ(self) -> int:
@@ -75,21 +87,29 @@ class Instance:
         return float(self.L) ** 3
 
     def save(self, path: str) -> None:
+        qp = {}
+        if self.qp_n:
+            qp = dict(qp_n=self.qp_n, qp_psi=self.qp_psi, qp_eps_ks=self.qp_eps_ks, qp_eps=self.qp_eps)
         np.savez(path, name=self.name, L=self.L, n_grid=self.n_grid, n2max=self.n2max,
                  miller=self.miller, psi=self.psi, eps=self.eps, v_loc=self.v_loc,
                  scissor=self.scissor, pdep=self.pdep, lam=self.lam,
                  overlap_thr=self.overlap_thr, keep_pairs=self.keep_pairs,
-                 spin=self.spin, seed=self.seed, n_eig=self.n_eig, block=self.block)
+                 spin=self.spin, seed=self.seed, n_eig=self.n_eig, block=self.block,
+                 n_up=self.n_up, **qp)
 
     @staticmethod
     def load(path: str) -> "Instance":
         d = np.load(path)
+        qp = {}
+        if "qp_n" in d:
+            qp = dict(qp_n=int(d["qp_n"]), qp_psi=d["qp_psi"], qp_eps_ks=d["qp_eps_ks"], qp_eps=d["qp_eps"])
         return Instance(name=str(d["name"]), L=float(d["L"]), n_grid=int(d["n_grid"]),
                         n2max=int(d["n2max"]), miller=d["miller"], psi=d["psi"],
                         eps=d["eps"], v_loc=d["v_loc"], scissor=float(d["scissor"]),
                         pdep=d["pdep"], lam=d["lam"], overlap_thr=float(d["overlap_thr"]),
                         keep_pairs=int(d["keep_pairs"]), spin=int(d["spin"]),
-                        seed=int(d["seed"]), n_eig=int(d["n_eig"]), block=int(d["block"]))
+                        seed=int(d["seed"]), n_eig=int(d["n_eig"]), block=int(d["block"]),
+                        n_up=int(d["n_up"]) if "n_up" in d else 0, **qp)
 
 
 # ----------------------------------------------------------------------------------
@@ -222,6 +242,11 @@ def _ground_state_tiny(L, miller, centres, depth, width, n_occ):
     return psi, e[:n_occ].copy()
 
 
+def _ks_states_tiny(L, miller, centres, depth, width, n_states):
+    """Lowest n_states eigenpairs (occupied and conduction) of the same model KS Hamiltonian."""
+    return _ground_state_tiny(L, miller, centres, depth, width, n_states)
+
+
 def _random_orthonormal_packed(rng, n_vec: int, n_pw: int) -> np.ndarray:
     """n_vec orthonormal Gamma-real vectors on S \\ {0} (columns 0 and 1 zero), FP64 QR."""
     X = rng.standard_normal((n_pw - 2, n_vec))
@@ -234,8 +259,18 @@ def _random_orthonormal_packed(rng, n_vec: int, n_pw: int) -> np.ndarray:
 def make_tiny(seed: int = 0, L: float = 8.0, N: int = 16, n2max: int = 14, n_occ: int = 4,
               n_wells: int = 4, depth: float = 2.0, width: float = 1.0,
               scissor: float = 0.03, overlap_thr: float = 1e-3, spin: int = 0,
-              n_eig: int = 4, block: int = 8) -> Instance:
-    """Plain FP64 tiny cell: L=8 bohr, 16^3 grid, 251 plane waves, 4 wells, full PDEP basis."""
+              n_eig: int = 4, block: int = 8, n_qp: int = 0, spin_pol=None) -> Instance:
+    """Plain FP64 tiny cell: L=8 bohr, 16^3 grid, 251 plane waves, 4 wells, full PDEP basis.
+
+    n_qp > n_occ adds explicit quasi-particle data for the lowest n_qp states (Eq. ham): their
+    KS states and energies from the same diagonalisation, and QP energies drawn as seeded
+    shifts of the KS ones (occupied -0.06..-0.04 Ha, conduction +0.05..+0.10 Ha), standing in
+    for G0W0 corrections (Fig. 1).
+
+    spin_pol = (n_up, n_dn) makes a spin-polarised system: the n_up lowest KS states occupied in
+    the up channel and the n_dn lowest in the down channel (one spin-independent model
+    Hamiltonian, as for a high-spin open shell).
+    """
     rng = np.random.default_rng(seed)
     centres = _draw_centres(rng, n_wells, L, 2.0)
     miller = sphere_half(n2max)
@@ -244,10 +279,24 @@ def make_tiny(seed: int = 0, L: float = 8.0, N: int = 16, n2max: int = 14, n_occ
     n_pw = psi.shape[1]
     pdep = _random_orthonormal_packed(rng, n_pw - 2, n_pw)
     lam = rng.uniform(-0.9, -0.01, n_pw - 2)
+    n_up = 0
+    if spin_pol is not None:
+        n_up, n_dn = int(spin_pol[0]), int(spin_pol[1])
+        st, e_ks = _ks_states_tiny(L, miller, centres, depth, width, max(n_up, n_dn))
+        psi = np.concatenate([st[:n_up], st[:n_dn]])
+        eps = np.concatenate([e_ks[:n_up], e_ks[:n_dn]])
+    qp = {}
+    if n_qp:
+        if n_qp <= n_occ:
+            raise ValueError("n_qp must exceed n_occ")
+        states, e_ks = _ks_states_tiny(L, miller, centres, depth, width, n_qp)
+        r2 = np.random.default_rng(10_000 + seed)
+        shift = np.concatenate([r2.uniform(-0.06, -0.04, n_occ), r2.uniform(0.05, 0.10, n_qp - n_occ)])
+        qp = dict(qp_n=n_qp, qp_psi=states[n_occ:].copy(), qp_eps_ks=e_ks, qp_eps=e_ks + shift)
     return Instance(name=f"tiny-L{L:g}-N{N}-s{seed}", L=L, n_grid=N, n2max=n2max,
                     miller=miller, psi=psi, eps=eps, v_loc=v_loc, scissor=scissor,
                     pdep=pdep, lam=lam, overlap_thr=overlap_thr, keep_pairs=0,
-                    spin=spin, seed=seed, n_eig=n_eig, block=block)
+                    spin=spin, seed=seed, n_eig=n_eig, block=block, n_up=n_up, **qp)
 
 
 # ----------------------------------------------------------------------------------
