@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 
 MEV = 3.6749322e-5
 N_EIG, BLOCK, MAX_SUB = 16, 32, 128
+# trial vectors the medium mixed solve passes through the operator (measured on the GPU);
+# the CPU reference arm scales its samples to this many applications
+N_APPLY_MEDIUM = 528
 TOL_MIXED, TOL_FP64 = 2e-4, 1e-5
 
 
@@ -49,7 +52,6 @@ def parse():
     ap.add_argument("--nvec", type=int, default=32)
     ap.add_argument("--batch", type=int, default=0,
                     help="solve this many uneven systems of the batch family together (bse_solve_batch)")
-    ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work per sample")
     return ap.parse_args()
 
 
@@ -104,58 +106,100 @@ class Clocks:
 # --------------------------------------------------------------------------------------
 # CPU oracle on a bounded sample (cpu_baseline leg and the reference arm)
 # --------------------------------------------------------------------------------------
-def cpu_oracle_setup(inst):
-    """Build the FP64 oracle operator once (orbitals on the grid, overlaps, pair mask)."""
-    from oracle import liouville
+def cpu_oracle_setup(inst, seed: int = 0):
+    """FP64 oracle set-up for the CPU baseline (not counted in the solve time): the operator
+    (orbitals on the grid, overlaps, pair mask) and, timed once, the per-vector work of one
+    operator application (one vector's orbitals to the grid and its Hartree potential)."""
+    import numpy as np
+    from oracle import liouville, pairs as opairs
     t0 = time.perf_counter()
     Lop = liouville.Liouville(inst)
-    return Lop, time.perf_counter() - t0
+    setup_s = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    A1 = Lop.project(rng.standard_normal((1, inst.n_occ, inst.n_pw)))
+    t0 = time.perf_counter()
+    ua, VH = Lop.fields(A1)
+    t_fixed = time.perf_counter() - t0
+    plist = opairs.pair_list(Lop.mask)
+    return dict(inst=inst, Lop=Lop, A1=A1, ua=ua, VH=VH, t_fixed=t_fixed, setup_s=setup_s,
+                plist=plist, P=int(plist.shape[0]), cores=len(os.sched_getaffinity(0)))
 
 
-def cpu_oracle_sample(inst, Lop, n_apply_vectors: int, budget_s: float, setup_s: float = 0.0):
-    """Time the FP64 oracle on a bounded sample of one solve and scale it to the whole solve.
+def cpu_oracle_step(S, i: int, n_apply_vectors: int, pairs_per_step: int = 4, rows_per_step: int = 2):
+    """One bounded sample of the FP64 oracle's solve, scaled to the whole solve.
 
-    Sample: tau_vw for the first pairs of the list (per-pair cost), the per-vector fixed work
-    of one operator application (inverse FFTs of all orbitals and the Hartree potential) and
-    the per-row work of up to three rows (K1d sum over the row's pairs, local and exchange
-    terms, forward FFT, P_c). One solve = P pairs + n_apply vectors x (fixed + N_occ rows).
+    Sample i times, with the oracle as it stands, tau_vw for `pairs_per_step` pairs spread
+    over the pair list (each computed afresh) and the K1d / local / exchange / forward
+    transform work of `rows_per_step` orbital rows of one vector (Liouville.apply_rows; the
+    rows' tau come from the cache or are built untimed first). With the per-vector work
+    t_fixed of the set-up, one solve is modelled as
+        P t_pair + n_apply (t_fixed + N_occ t_row),
+    the same sum the solve performs (every pair's tau once, every applied vector through
+    every row), checked against a timed complete oracle solve of a small system.
     """
     import numpy as np
-    from oracle import pairs as opairs
-    from oracle.basis import packed_to_grid_field
-    cores = len(os.sched_getaffinity(0))
-    mask = Lop.mask
-    P = int(np.triu(mask).sum())
-    plist = opairs.pair_list(mask)
-    Lop._tau.clear()
-    k = 0
+    Lop, P, plist, inst = S["Lop"], S["P"], S["plist"], S["inst"]
+    n = inst.n_occ
+    stride = max(1, P // 97)
+    t_pair = 0.0
+    for q in range(pairs_per_step):
+        v, w = (int(x) for x in plist[((i * pairs_per_step + q) * stride) % P])
+        Lop._tau.pop((v, w), None)
+        t0 = time.perf_counter()
+        Lop.tau(v, w)
+        t_pair += time.perf_counter() - t0
+    t_pair /= pairs_per_step
+    rows = [((i * rows_per_step + q) * 37) % n for q in range(rows_per_step)]
+    for v in rows:
+        for w in np.nonzero(Lop.mask[v])[0]:
+            Lop.tau(v, int(w))
     t0 = time.perf_counter()
-    while k < min(64, P) and (time.perf_counter() - t0) < 0.3 * budget_s:
-        Lop.tau(int(plist[k, 0]), int(plist[k, 1]))
-        k += 1
-    t_pair = (time.perf_counter() - t0) / max(k, 1)
-    rng = np.random.default_rng(0)
-    A = Lop.project(rng.standard_normal((1, inst.n_occ, inst.n_pw)))
+    Lop.apply_rows(S["A1"], S["ua"], S["VH"], rows)
+    t_row = (time.perf_counter() - t0) / rows_per_step
+    value = P * t_pair + n_apply_vectors * (S["t_fixed"] + n * t_row)
+    return dict(value=value, t_pair_s=t_pair, t_row_s=t_row)
+
+
+def cpu_model_check(seed: int = 0):
+    """Times a complete FP64 oracle solve (tau build + block Davidson to 1e-5 Ha) of a small
+    localised system (32^3 grid, 16 orbitals, 4 excitations) and the model's prediction for
+    it from the same kind of samples: (measured s, predicted s)."""
+    import numpy as np
+    from synth import make_localized
+    from oracle import davidson
+    inst = make_localized(6, 20.0 * 32 / 72, 32, 16, 2.5, 32, n_eig=4, block=4)
+    S = cpu_oracle_setup(inst, seed)
+    S["Lop"]._tau.clear()
+    Lop = S["Lop"]
     t0 = time.perf_counter()
-    ua = packed_to_grid_field(A, inst.miller, inst.n_grid)
-    Lop.hartree(ua)
-    t_fixed = time.perf_counter() - t0
-    rows = [v for v in range(inst.n_occ)
-            if all((min(v, w), max(v, w)) in Lop._tau for w in np.nonzero(mask[v])[0])][:3]
-    if not rows:
-        rows = [0]
-        for w in np.nonzero(mask[0])[0]:
-            Lop.tau(0, int(w))
-    t0 = time.perf_counter()
-    Lop.apply(A, rows=rows)
-    t_rows = time.perf_counter() - t0 - t_fixed        # apply() redoes the fixed work
-    t_row = max(t_rows, 0.0) / len(rows)
-    t_solve = P * t_pair + n_apply_vectors * (t_fixed + inst.n_occ * t_row)
-    sample = (f"oracle FP64 on {k} tau pairs (of {P}), one vector's inverse FFTs + Hartree, "
-              f"{len(rows)} operator rows; scaled to {P} pairs + {n_apply_vectors} vectors x "
-              f"{inst.n_occ} rows; one-time oracle set-up {setup_s:.1f} s not counted")
-    return dict(value=t_solve, unit="s", cores=cores, kind="oracle", sample=sample,
-                t_pair_s=t_pair, t_vec_fixed_s=t_fixed, t_row_s=t_row)
+    Lop.build_tau()
+    om, _, info = davidson.davidson(Lop.apply, Lop.diagonal(), Lop.project, 4, 4, 32, 1e-5)
+    measured = time.perf_counter() - t0
+    n_apply = int(info.get("n_apply", 0)) or None
+    preds = [cpu_oracle_step(S, i, n_apply or 1)["value"] for i in range(4)]
+    return measured, float(np.median(preds)), n_apply
+
+
+def cpu_baseline_run(inst, n_apply_vectors: int, steps: int, warmup: int = 0):
+    """Set-up, then `warmup` + `steps` samples; returns the baseline entry (value = mean of
+    the timed samples, with their spread) and the per-sample values."""
+    import numpy as np
+    S = cpu_oracle_setup(inst)
+    vals = []
+    for i in range(warmup + steps):
+        r = cpu_oracle_step(S, i, n_apply_vectors)
+        if i >= warmup:
+            vals.append(r["value"])
+    meas, pred, nap = cpu_model_check()
+    v = float(np.mean(vals))
+    sample = (f"FP64 oracle, {steps} samples of 4 tau pairs (of {S['P']}) + 2 operator rows (of "
+              f"{inst.n_occ}) each, with one vector's grid transforms + Hartree ({S['t_fixed']:.2f} s, "
+              f"timed once); scaled to {S['P']} pairs + {n_apply_vectors} vectors x {inst.n_occ} rows. "
+              f"Model check on a complete oracle solve (32^3, 16 orbitals, {nap} vectors): "
+              f"measured {meas:.2f} s, model {pred:.2f} s. Oracle set-up {S['setup_s']:.1f} s not counted")
+    return {"value": v, "unit": "s", "cores": S["cores"], "kind": "oracle", "sample": sample,
+            "spread": {"min": float(np.min(vals)), "max": float(np.max(vals)), "n": len(vals)},
+            "model_check": {"measured_s": meas, "model_s": pred}}
 
 
 # --------------------------------------------------------------------------------------
@@ -264,20 +308,12 @@ def main():
         if rank != 0:
             return
         inst = probe
-        Lop, setup_s = cpu_oracle_setup(inst)
-        vals = []
-        for i in range(args.warmup + args.steps):
-            r = cpu_oracle_sample(inst, Lop, n_apply_vectors=530, budget_s=args.cpu_budget,
-                                  setup_s=setup_s)
-            if i >= args.warmup:
-                vals.append(r)
-        v = sum(x["value"] for x in vals) / len(vals)
+        base = cpu_baseline_run(inst, N_APPLY_MEDIUM, steps=args.steps, warmup=args.warmup)
+        v = base["value"]
         line = {"impl": "reference", "metric": metric, "value": v, "unit": "s", "n_gpus": 0,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": cfg_desc,
-                "cpu_baseline": {"value": v, "unit": "s", "cores": vals[0]["cores"],
-                                 "kind": "oracle", "sample": vals[0]["sample"]},
+                "data": "synthetic", "config": cfg_desc, "cpu_baseline": base,
                 "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -351,10 +387,10 @@ def main():
     t_launch = d["ms"] / nl * 1e-3
     bytes_launch = d["bytes"] / d["calls"] if name not in per_kernel_launches else d["bytes"] / d["calls"]
     achieved = bytes_launch / t_launch / 1e9
-    # DRAM traffic per launch of the K1d kernel: its entry-major tau (four slots per entry of
-    # the row-block neighbour lists) once, a(r) and the result once, V_loc, V_H and u_psi.
-    # The ncu capture of the op256 launch (32 vectors, 32^3 grid) read and wrote 4.311 GB
-    # where this model gives 4.331 GB; the algorithmic bytes count tau once per pair.
+    # DRAM traffic per launch of the K1d kernel (model): its entry-major tau once (four slots
+    # per entry of the row-block neighbour lists), a(r) and the result once, V_loc, V_H and
+    # u_psi. The ncu capture of the op256 launch (32 vectors, 32^3 grid) read and wrote 4.311
+    # GB where this model gives 4.331 GB; the algorithmic bytes count tau once per pair.
     traffic = None
     if name == "k1d_combine":
         pr = ctx.pairs()
@@ -407,10 +443,7 @@ def main():
 
     cpu = None
     if not args.no_cpu and rank == 0:
-        Lop, setup_s = cpu_oracle_setup(inst)
-        cpu = cpu_oracle_sample(inst, Lop, n_apply_vectors=stats[-1].n_apply, budget_s=args.cpu_budget,
-                                setup_s=setup_s)
-        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu = cpu_baseline_run(inst, stats[-1].n_apply, steps=3)
 
     if rank == 0:
         line = {"metric": metric, "value": ms / 1e3, "unit": "s", "n_gpus": world,

@@ -25,9 +25,11 @@
  *  - v(G) = 4 pi/|G|^2 for G != 0, v(0) = 0, and the head term Xi of Eq. (pdep) is 0.
  *
  * Ownership: the caller owns every pointer it passes; input arrays are read during
- * the call only. The context owns its device buffers (tau, plans, workspaces),
- * obtained with cudaMalloc, released by bse_destroy. All device work is ordered on
- * the stream given to bse_create; calls return after that work has completed.
+ * the call only. The context owns its device buffers (tau, plans, workspaces); it
+ * obtains every one of them from the allocator given to bse_create (or, without one,
+ * from cudaMallocAsync on the context stream) and returns them before bse_destroy
+ * returns. All device work is ordered on the stream given to bse_create; calls return
+ * after that work has completed.
  *
  * Errors: every call returns a bse_status. On error no output is valid (except
  * BSE_ERR_NOT_CONVERGED, see bse_davidson) and bse_last_error() describes it. The
@@ -79,11 +81,45 @@ typedef struct {
   double overlap_thr;      /* > 0: keep tau_vw iff O_vw >= overlap_thr (Eq. overlap) */
   int64_t keep_pairs;      /* used when overlap_thr <= 0: number of v <= w pairs to keep */
   int spin;                /* 0 singlet (K1e factor 2, Eq. k1e), 1 triplet (factor 0) */
+  /* Explicit quasi-particle energies (Eq. ham). n_qp = 0: the scissor form above. n_qp > n_occ:
+   * H_QP = H_KS + sum_{n <= N_QP} |psi_n>(eps^QP_n - eps_n - Delta)<psi_n| + Delta, with
+   * Delta the mean of eps^QP_n - eps_n over n = N_mid..N_QP, N_mid = (N_occ + N_QP) / 2
+   * (1-based, integer division); eps^QP_v replaces eps_v in D and `eps`, `scissor` are
+   * ignored. */
+  int n_qp;
+  const double* qp_psi;    /* [n_qp - n_occ][2*n_half] packed KS states n_occ+1..N_QP (orthonormal,
+                              orthogonal to psi); the occupied terms of the sum vanish under P_c */
+  const double* qp_eps_ks; /* [n_qp] KS energies eps_n of states 1..N_QP (Ha) */
+  const double* qp_eps;    /* [n_qp] QP energies eps^QP_n of states 1..N_QP (Ha) */
+  /* Spin-polarised systems with spin-conserving excitations (Section 2: the paper's code
+   * supports them; Eqs. evp-k1d are written for one channel). n_up = 0: closed shell. n_up > 0:
+   * orbitals [0, n_up) of psi/eps are spin up and [n_up, n_occ) spin down, each its own
+   * spin-orbital; each channel has its own projector P_c (occupied orbitals of that channel),
+   * K1e couples both channels through the Hartree potential of the total density change with
+   * factor 1 (`spin` is ignored), and tau_vw (K1d) is kept only within a channel. Both
+   * channels share v_loc and the PDEP basis. */
+  int n_up;
 } bse_system;
 
+/* Caller-supplied device allocator (e.g. the PyTorch caching allocator). alloc returns
+ * `bytes` of device memory on the current device, aligned to at least 256 bytes, or NULL
+ * when it cannot (the call then fails with BSE_ERR_OOM); free returns a block obtained from
+ * alloc. Both are called from the thread that makes the library call (for bse_solve_batch,
+ * from one worker thread per context, possibly at the same time) and in the order of the
+ * context stream: a freed block may still be read by work already queued on that stream,
+ * so the allocator may hand it out again only to work ordered after it on that stream, as a
+ * stream-ordered or caching allocator bound to that stream does. `user` is passed through. */
+typedef void* (*bse_alloc_fn)(size_t bytes, void* user);
+typedef void (*bse_free_fn)(void* ptr, void* user);
+
 /* Create a context: validates the system, uploads it, computes psi_v(r).
- * stream: a cudaStream_t (NULL = legacy default stream). Device = current device. */
-int bse_create(const bse_system* sys, int precision, void* stream, bse_ctx** out);
+ * alloc_fn, free_fn: the device allocator for every buffer the context owns; both NULL
+ * selects cudaMallocAsync / cudaFreeAsync on the context stream; exactly one NULL is
+ * BSE_ERR_INVALID_ARG. user: passed to both. stream: a cudaStream_t (NULL = legacy
+ * default stream). Device = current device. On failure *out may hold a context that
+ * only carries the error text (bse_last_error); release it with bse_destroy. */
+int bse_create(const bse_system* sys, int precision, bse_alloc_fn alloc_fn, bse_free_fn free_fn,
+               void* user, void* stream, bse_ctx** out);
 
 /* Overlaps O_vw (Eq. overlap, grid quadrature of FP64 densities, accumulated in float-float
  * arithmetic to about 1e-14 relative, in both precision modes), the pair rule, and the screened
@@ -108,17 +144,17 @@ int bse_get_overlaps(const bse_ctx* ctx, double* o_out);
 int bse_apply_liouville(bse_ctx* ctx, int n_vec, const void* a_in, void* a_out);
 
 /* The same operator as bse_apply_liouville, for callers that cannot allocate device
- * memory at call time: code running while a CUDA graph is captured, processes whose
- * device memory is handed out by an external pool, or latency-critical paths where an
- * allocation (which may synchronise the device) is not allowed. The paper has no
- * counterpart; this is a library addition.
+ * memory at call time: processes whose device memory is handed out by an external pool
+ * with a fixed budget, or latency-critical paths where an allocation (which may
+ * synchronise the device) is not allowed. The paper has no counterpart; this is a
+ * library addition.
  *
  * The r-space workspaces of the call live in one fixed 32 MiB array compiled into the
  * library (every GPU that loads the library holds it until the process exits). No
  * cudaMalloc, cudaFree or allocating library routine is called; the context must
  * still have been created and bse_build_tau run. Limit: 2 * ceil(n_vec*n_occ/2) + 
- * ceil(n_vec/2) complex grids of N^3 points plus n_vec*n_occ*n_occ projector
- * coefficients (each part rounded up to 256 bytes) must fit in 32 MiB; larger requests
+ * ceil(n_vec/2) complex grids of N^3 points plus n_vec*n_occ*max(n_occ, n_qp - n_occ)
+ * projector coefficients (each part rounded up to 256 bytes) must fit in 32 MiB; larger requests
  * return BSE_ERR_INVALID_ARG with the byte count in bse_last_error(). The projector
  * runs on the SIMT GEMM in both precisions.
  *
@@ -157,6 +193,45 @@ typedef struct {
  * On BSE_ERR_NOT_CONVERGED omega_out, vec_out and stats hold the last Ritz pairs. */
 int bse_davidson(bse_ctx* ctx, const bse_davidson_opts* opts, double* omega_out,
                  void* vec_out, bse_davidson_stats* stats);
+
+/* Wannier localisation of the occupied orbitals (Section 2, Eqs. wannier and spread): the
+ * orthogonal U that jointly diagonalises, approximately, the six matrices
+ * A^(n)_vw = <psi_v|M^(n)|psi_w>, M = cos(2 pi x/L), sin(2 pi x/L), cos(2 pi y/L), ... (JADE),
+ * i.e. minimises sigma^2(U) = sum_n [Tr(U^T B^(n) U) - sum_v ((U^T A^(n) U)_vv)^2]. U starts
+ * from the eigenvectors of A^(1) (sweeps on A^(1) alone), then sweeps of Givens rotations on
+ * all six run until every rotation has |sin| <= tol or max_sweeps is reached. The context
+ * then works in the localised frame: its orbitals become psi~_v = sum_w U_wv psi_w, so that
+ * the overlap rule (Eq. overlap) and tau act on localised orbitals, and the occupied energies
+ * of D (Eq. d) become the matrix E = U^T diag(eps) U (D a_v = P_c H a_v - sum_w E_vw a_w);
+ * excitation energies are unchanged, eigenvectors come out in the localised frame (rotate
+ * back with U). Must run before bse_build_tau; closed-shell systems only. Outputs
+ * (nullable): U_out host [n_occ][n_occ] (column v = coefficients of psi~_v), spread_out
+ * host [2] = sigma^2 before and after. */
+int bse_localize(bse_ctx* ctx, int max_sweeps, double tol, double* U_out, double* spread_out);
+
+/* Lanczos chains for the optical absorption spectrum (Section 4: the spectrum of bulk Si is
+ * computed with a Lanczos recursion of N_Lanczos applications of the Liouville operator per
+ * polarisation direction, instead of an iterative diagonalisation). For each direction
+ * dirs[p] (0 = x, 1 = y, 2 = z), p < n_pol <= 3, the chain starts from the dipole block
+ * d_v = P_c(-d psi_v / d r_i), v = 1..N_occ (the commutator [H, r_i] of the local
+ * Hamiltonian acting on the occupied orbitals; velocity form), and runs
+ *   w = L q_k - beta_k q_{k-1}, alpha_k = <q_k|w>, w -= alpha_k q_k, w <- P_c w,
+ *   beta_{k+1} = |w|, q_{k+1} = w / beta_{k+1}
+ * for n_steps applications of the operator, the directions together as one block on the
+ * device. Outputs (host, FP64): alpha_out, beta_out [n_pol][n_steps] (beta[p][0] = 0;
+ * beta[p][k] couples steps k-1 and k; after a breakdown, beta = 0, the chain continues with
+ * zeros), norm2_out [n_pol] = |d|^2. The vectors are in the context precision; the
+ * coefficients are accumulated in FP64. Requires bse_build_tau first. */
+int bse_lanczos(bse_ctx* ctx, int n_pol, const int* dirs, int n_steps, double* alpha_out, double* beta_out,
+                double* norm2_out);
+
+/* Spectral function of one chain on the GPU: g(omega + i eta) = <d|(omega + i eta - L)^{-1}|d>
+ * = norm2 / (z - alpha_0 - beta_1^2 / (z - alpha_1 - beta_2^2 / ...)) for n_omega
+ * frequencies (Ha), eta > 0 the broadening; the absorption line shape is -Im g / pi.
+ * alpha, beta: one chain's n_steps coefficients as returned by bse_lanczos; all arrays are
+ * host FP64; g_re, g_im: host [n_omega]. Uses the context's stream and allocator only. */
+int bse_lanczos_spectrum(bse_ctx* ctx, int n_steps, const double* alpha, const double* beta, double norm2,
+                         int n_omega, const double* omega, double eta, double* g_re, double* g_im);
 
 /* Batched solves (library addition; the paper distributes one system over many GPUs,
  * Section 3): for each of n independent contexts -- typically many small systems of

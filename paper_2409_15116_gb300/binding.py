@@ -27,7 +27,8 @@ EXPORTS = ["bse_create", "bse_build_tau", "bse_get_pairs", "bse_get_overlaps",
            "bse_apply_liouville", "bse_davidson", "bse_last_error", "bse_version",
            "bse_destroy", "bse_profile", "bse_profile_read", "bse_apply_liouville_static",
            "bse_precond_collect", "bse_precond_set_samples", "bse_precond_grad",
-           "bse_precond_train", "bse_precond_load", "bse_solve_batch"]
+           "bse_precond_train", "bse_precond_load", "bse_solve_batch", "bse_lanczos",
+           "bse_lanczos_spectrum", "bse_localize"]
 NPARAM = 4619
 
 
@@ -44,7 +45,9 @@ class System(C.Structure):
                 ("v_loc", C.POINTER(C.c_double)), ("scissor", C.c_double),
                 ("n_pdep", C.c_int), ("pdep", C.POINTER(C.c_double)),
                 ("lam", C.POINTER(C.c_double)), ("overlap_thr", C.c_double),
-                ("keep_pairs", C.c_int64), ("spin", C.c_int)]
+                ("keep_pairs", C.c_int64), ("spin", C.c_int), ("n_qp", C.c_int),
+                ("qp_psi", C.POINTER(C.c_double)), ("qp_eps_ks", C.POINTER(C.c_double)),
+                ("qp_eps", C.POINTER(C.c_double)), ("n_up", C.c_int)]
 
 
 class ProfEntry(C.Structure):
@@ -63,6 +66,43 @@ class DavidsonStats(C.Structure):
                 ("precond_fallbacks", C.c_int)]
 
 
+# caller-supplied device allocator of bse_create (include/bse.h: bse_alloc_fn, bse_free_fn)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class TorchAllocator:
+    """Device memory of one context from PyTorch's caching allocator, bound to the context
+    stream (so a block the library frees is reused only by work ordered after it on that
+    stream). Records the blocks it hands out: ``live`` (pointer -> bytes) and ``total``."""
+
+    def __init__(self, stream_handle: int, device: int):
+        import torch
+        self.stream = int(stream_handle)
+        self.device = int(device)
+        self.live = {}
+        self.total = 0
+        self.calls = 0
+
+        def _alloc(nbytes, _user):
+            try:
+                p = torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+            except Exception:       # out of memory: the library reports BSE_ERR_OOM
+                return None
+            self.live[int(p)] = int(nbytes)
+            self.total += int(nbytes)
+            self.calls += 1
+            return int(p)
+
+        def _free(ptr, _user):
+            if ptr:
+                torch.cuda.caching_allocator_delete(int(ptr))
+                self.live.pop(int(ptr), None)
+
+        self.alloc_fn = ALLOC_FN(_alloc)
+        self.free_fn = FREE_FN(_free)
+
+
 _lib = None
 
 
@@ -75,7 +115,7 @@ def load(path: str = LIB_PATH):
         raise ImportError(f"{path} not found: build it with paper_2409_15116_gb300.build.build()")
     lib = C.CDLL(path)
     P = C.c_void_p
-    lib.bse_create.argtypes = [C.POINTER(System), C.c_int, P, C.POINTER(P)]
+    lib.bse_create.argtypes = [C.POINTER(System), C.c_int, ALLOC_FN, FREE_FN, P, P, C.POINTER(P)]
     lib.bse_build_tau.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
     lib.bse_get_pairs.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.bse_get_overlaps.argtypes = [P, C.POINTER(C.c_double)]
@@ -98,6 +138,9 @@ def load(path: str = LIB_PATH):
     lib.bse_precond_load.argtypes = [P, F]
     lib.bse_solve_batch.argtypes = [C.POINTER(P), C.c_int, C.POINTER(DavidsonOpts), C.POINTER(C.c_double),
                                     C.POINTER(DavidsonStats), C.POINTER(C.c_int)]
+    lib.bse_lanczos.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.c_int, D, D, D]
+    lib.bse_localize.argtypes = [P, C.c_int, C.c_double, D, D]
+    lib.bse_lanczos_spectrum.argtypes = [P, C.c_int, D, D, C.c_double, C.c_int, D, C.c_double, D, D]
     lib.bse_destroy.argtypes = [P]
     lib.bse_destroy.restype = None
     for name in EXPORTS:
@@ -122,10 +165,21 @@ class Stats:
 
 class Context:
     """One system on the current CUDA device; ``sys`` is any object with the instance fields
-    (L, n_grid, miller, psi, eps, v_loc, scissor, pdep, lam, overlap_thr, keep_pairs, spin)."""
+    (L, n_grid, miller, psi, eps, v_loc, scissor, pdep, lam, overlap_thr, keep_pairs, spin).
 
-    def __init__(self, sys, precision: int = PREC_FP64, stream=None):
+    allocator: "torch" (default) hands the context's device memory out of PyTorch's caching
+    allocator through the bse_create callbacks; None lets the library use cudaMallocAsync."""
+
+    def __init__(self, sys, precision: int = PREC_FP64, stream=None, allocator="torch"):
         self.lib = load()
+        self.allocator = None
+        if allocator == "torch":
+            import torch
+            torch.cuda.empty_cache()     # cached blocks of earlier contexts count as free memory
+            self.allocator = TorchAllocator(int(stream) if stream is not None else 0,
+                                            torch.cuda.current_device())
+        elif allocator is not None:
+            raise ValueError("allocator must be 'torch' or None")
         self.precision = precision
         self._keep = []
         miller = np.ascontiguousarray(sys.miller, dtype=np.int32)
@@ -135,16 +189,28 @@ class Context:
         pdep = np.ascontiguousarray(sys.pdep, dtype=np.float64)
         lam = np.ascontiguousarray(sys.lam, dtype=np.float64)
         self._keep += [miller, psi, eps, vloc, pdep, lam]
+        n_qp = int(getattr(sys, "qp_n", 0) or 0)
+        qp = {}
+        if n_qp:
+            qpsi = np.ascontiguousarray(sys.qp_psi, dtype=np.float64)
+            qks = np.ascontiguousarray(sys.qp_eps_ks, dtype=np.float64)
+            qe = np.ascontiguousarray(sys.qp_eps, dtype=np.float64)
+            self._keep += [qpsi, qks, qe]
+            qp = dict(qp_psi=_dptr(qpsi), qp_eps_ks=_dptr(qks), qp_eps=_dptr(qe))
         s = System(n_grid=int(sys.n_grid), L=float(sys.L), n_half=int(miller.shape[0]),
                    miller=miller.ctypes.data_as(C.POINTER(C.c_int32)), n_occ=int(psi.shape[0]),
                    psi=_dptr(psi), eps=_dptr(eps), v_loc=_dptr(vloc), scissor=float(sys.scissor),
                    n_pdep=int(pdep.shape[0]), pdep=_dptr(pdep), lam=_dptr(lam),
                    overlap_thr=float(sys.overlap_thr), keep_pairs=int(sys.keep_pairs),
-                   spin=int(sys.spin))
+                   spin=int(sys.spin), n_qp=n_qp, n_up=int(getattr(sys, "n_up", 0) or 0), **qp)
         self.n_occ, self.n_pw = psi.shape
         h = C.c_void_p()
         st = C.c_void_p(int(stream) if stream is not None else 0)
-        rc = self.lib.bse_create(C.byref(s), precision, st, C.byref(h))
+        if self.allocator is not None:
+            af, ff = self.allocator.alloc_fn, self.allocator.free_fn
+        else:
+            af, ff = ALLOC_FN(), FREE_FN()
+        rc = self.lib.bse_create(C.byref(s), precision, af, ff, None, st, C.byref(h))
         self.h = h
         if rc != BSE_OK:
             msg = self.lib.bse_last_error(h).decode() if h else "bse_create failed"
@@ -186,6 +252,9 @@ class Context:
         return out, int(nl.value)
 
     def build_tau(self):
+        if self.allocator is not None:
+            import torch
+            torch.cuda.empty_cache()     # the tau layout is chosen from the free device memory
         n = C.c_int64()
         t = C.c_double()
         self._check(self.lib.bse_build_tau(self.h, C.byref(n), C.byref(t)))
@@ -212,6 +281,39 @@ class Context:
                                                  C.c_void_p(a_in.data_ptr()),
                                                  C.c_void_p(a_out.data_ptr())))
         return a_out
+
+    # ---- Wannier localisation ----
+    def localize(self, max_sweeps=100, tol=1e-10):
+        """JADE localisation of the context's orbitals (before build_tau): (U, spread before,
+        spread after); the context continues in the localised frame."""
+        U = np.zeros((self.n_occ, self.n_occ))
+        sp = np.zeros(2)
+        self._check(self.lib.bse_localize(self.h, int(max_sweeps), float(tol), _dptr(U), _dptr(sp)))
+        return U, float(sp[0]), float(sp[1])
+
+    # ---- absorption spectrum ----
+    def lanczos(self, n_steps, dirs=(0, 1, 2)):
+        """Lanczos chains from the dipole blocks of the given directions: (alpha, beta, norm2)
+        with alpha, beta [n_pol, n_steps] and norm2 [n_pol]."""
+        d = np.ascontiguousarray(dirs, dtype=np.int32)
+        npol = int(d.size)
+        a = np.zeros((npol, n_steps))
+        b = np.zeros((npol, n_steps))
+        n2 = np.zeros(npol)
+        self._check(self.lib.bse_lanczos(self.h, npol, d.ctypes.data_as(C.POINTER(C.c_int)), int(n_steps),
+                                         _dptr(a), _dptr(b), _dptr(n2)))
+        return a, b, n2
+
+    def lanczos_spectrum(self, alpha, beta, norm2, omega, eta):
+        """g(omega + i eta) of one chain, complex [n_omega] (computed on the GPU)."""
+        a = np.ascontiguousarray(alpha, dtype=np.float64)
+        b = np.ascontiguousarray(beta, dtype=np.float64)
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        gr = np.zeros(om.size)
+        gi = np.zeros(om.size)
+        self._check(self.lib.bse_lanczos_spectrum(self.h, int(a.size), _dptr(a), _dptr(b), float(norm2),
+                                                  int(om.size), _dptr(om), float(eta), _dptr(gr), _dptr(gi)))
+        return gr + 1j * gi
 
     # ---- learned preconditioner ----
     def precond_collect(self, n_eig, block, max_sub, max_it=200, res_tol=1e-6, ref_eig=32,

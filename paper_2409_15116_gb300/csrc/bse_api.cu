@@ -4,6 +4,7 @@
 #include "kernels.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -12,9 +13,11 @@
 #include <functional>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <queue>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 using namespace bse;
@@ -73,13 +76,25 @@ struct bse_ctx {
   Prof prof;
   // tensor-core (BF16x3) operands of the mixed path
   bool tc_ok = false;
-  Split psi_s, psiT_s, pdep_s, pdepT_s;
+  Split psi_s, psiT_s, pdep_s, pdepT_s, qpsi_s, qpsiT_s;
+  // explicit QP terms of D (Eq. ham): conduction KS states n_occ+1..N_QP and their delta_c
+  int n_qc = 0;
+  double *qpsi64 = nullptr, *qdelta = nullptr;
+  float* qpsi32 = nullptr;
+  // occupied energies as a matrix after a localising rotation (bse_localize): E = U^T diag(eps) U;
+  // its diagonal sits in eps / esh, the rest (E_off) enters D as - sum_w E_vw a_w
+  bool has_emat = false;
+  double* eoff64 = nullptr;
+  float* eoff32 = nullptr;
+  double spread0 = 0, spread1 = 0;
   void *ws_ahi = nullptr, *ws_alo = nullptr, *ws_bhi = nullptr, *ws_blo = nullptr;
   long ws_split_rows = 0;
   // TMA maps of the split workspace, by (base pointer, leading dimension); they span the
   // workspace's full row capacity, so they stay valid until it is reallocated
   std::map<std::pair<const void*, long>, TMap> ws_maps;
   int* d_err = nullptr;
+  // polls of each tensor-core pipeline wait before it gives up (BSE_TC_WAIT_LIMIT; -1 default)
+  long long tc_wait_limit = -1;
   // learned preconditioner: inference weights and training samples
   float* lp_params = nullptr;
   int* d_bad = nullptr;
@@ -92,9 +107,19 @@ struct bse_ctx {
   int n_half = 0, n_pw = 0, n_occ = 0, n_pdep = 0, spin = 0, prec = 0;
   int64_t keep_pairs = 0;
   cudaStream_t st = nullptr;
+  // caller-supplied device allocator (both null: cudaMallocAsync on the context stream)
+  bse_alloc_fn ua = nullptr;
+  bse_free_fn uf = nullptr;
+  void* uu = nullptr;
   std::string err = "no error";
   std::vector<double> g2p_h, eps_h, O_h;
-  std::vector<double> occw_h;  // per packed coordinate j: sum_v psi_v(j)^2 (occupied weight)
+  std::vector<double> gcart_h;  // [3][n_pw]: Cartesian G components per packed coordinate
+  // per spin channel and packed coordinate j: sum_{v in channel} psi_v(j)^2 (occupied weight)
+  std::vector<double> occw_h;
+  int n_up = 0;                // spin-polarised: orbitals [0, n_up) up, [n_up, n_occ) down; 0 closed shell
+  int chan(int v) const { return (n_up > 0 && v >= n_up) ? 1 : 0; }
+  // K1e factor of Eq. (k1e): 2 closed-shell singlet, 0 triplet, 1 per spin-orbital when polarised
+  double k1e_factor() const { return n_up > 0 ? 1.0 : (spin == 0 ? 2.0 : 0.0); }
   std::vector<int32_t> pv_h, pw_h;
   double thr = 0;
   bool tau_ready = false;
@@ -118,7 +143,9 @@ struct bse_ctx {
   int n_rblocks = 0;
   int64_t n_ent = 0;
   bool tau_entry = false;    // tau stored entry-major for the tiled K1d kernel
-  int k1d_sc = 0;            // K1d tile variant chosen by the autotuner (0: not tuned yet)
+  // K1d tile variant per block width n_vec, chosen by the autotuner (absent: not tuned yet)
+  std::map<int, int> k1d_var;
+  int k1d_force = 0;         // BSE_K1D_VARIANT: one variant for every width, no tuning
   bool autotune = true;
   int64_t n_pairs = 0, nnz = 0;
   void* tau = nullptr;       // entry-major (tau_entry) or per pair, point-tiled
@@ -147,29 +174,49 @@ int cuda_fail(bse_ctx* c, cudaError_t e, const char* what) {
     if (_e != cudaSuccess) return cuda_fail(c, _e, #call);   \
   } while (0)
 
-// Device allocations are stream-ordered on the context stream, so independent contexts
-// (e.g. a batch of systems on separate streams) never wait on each other's allocations.
+// Every device buffer of a context comes from here: from the caller's allocator when one
+// was given to bse_create, else stream-ordered on the context stream, so independent
+// contexts (e.g. a batch of systems on separate streams) never wait on each other's
+// allocations.
 template <typename T>
 int dalloc(bse_ctx* c, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), c->st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    char buf[256];
-    snprintf(buf, sizeof(buf), "device allocation of %zu bytes failed: %s", count * sizeof(T),
-             cudaGetErrorString(e));
-    c->err = buf;
-    return BSE_ERR_OOM;
+  const size_t bytes = count * sizeof(T);
+  if (c->ua) {
+    void* q = c->ua(bytes, c->uu);
+    if (!q || ((uintptr_t)q & 255)) {
+      if (q) c->uf(q, c->uu);
+      char buf[256];
+      snprintf(buf, sizeof(buf), "the caller's allocator %s for %zu bytes",
+               q ? "returned a block not aligned to 256 bytes" : "returned NULL", bytes);
+      c->err = buf;
+      return BSE_ERR_OOM;
+    }
+    *p = (T*)q;
+  } else {
+    cudaError_t e = cudaMallocAsync((void**)p, bytes, c->st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      char buf[256];
+      snprintf(buf, sizeof(buf), "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+      c->err = buf;
+      return BSE_ERR_OOM;
+    }
   }
   c->allocs.push_back(*p);
   return BSE_OK;
+}
+void dfree_raw(bse_ctx* c, void* p) {
+  if (c->uf) c->uf(p, c->uu);
+  else cudaFreeAsync(p, c->st);
 }
 void dfree(bse_ctx* c, void* p) {
   if (!p) return;
   auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
   if (it != c->allocs.end()) c->allocs.erase(it);
-  cudaFreeAsync(p, c->st);
+  dfree_raw(c, p);
 }
 struct Scope {
   bse_ctx* c; int id = -1; cudaEvent_t a = nullptr; double bytes, flops;
@@ -221,7 +268,7 @@ int ensure_split_ws(bse_ctx* c, long rows) {
   dfree(c, c->ws_ahi); dfree(c, c->ws_alo); dfree(c, c->ws_bhi); dfree(c, c->ws_blo);
   c->ws_ahi = c->ws_alo = c->ws_bhi = c->ws_blo = nullptr;
   c->ws_split_rows = 0;
-  const long ldk = pad8(c->n_pw), lds = pad8(std::max(c->n_occ, std::max(1, c->n_pdep)));
+  const long ldk = pad8(c->n_pw), lds = pad8(std::max(std::max(c->n_occ, c->n_qc), std::max(1, c->n_pdep)));
   unsigned short* p;
   CA(dalloc(c, &p, (size_t)rows * ldk)); c->ws_ahi = p;
   CA(dalloc(c, &p, (size_t)rows * ldk)); c->ws_alo = p;
@@ -259,7 +306,7 @@ int tc_product(bse_ctx* c, const float* X, long M, long K, long ldx, const Split
   int splits = 1;
   if (beta == 0.0 && tiles < 2 * 152) splits = (int)std::min<long>(std::max<long>(1, 304 / tiles), std::max<long>(1, kt / 4));
   CK(tc_gemm_bf16x3(mh.b, ml.b, B.mhi.b, B.mlo.b, (int)M, (int)B.rows, (int)K, alpha, beta, out, ldo,
-                    splits, c->d_err, c->st));
+                    splits, c->d_err, c->st, c->tc_wait_limit));
   return BSE_OK;
 }
 
@@ -321,6 +368,7 @@ int project(bse_ctx* c, long rows, T* X, T* cbuf) {
     if (c->tc_ok) {
       // C = X Psi^T (BF16x3 tensor cores), X -= C Psi
       CA(tc_product(c, (const float*)X, rows, c->n_pw, c->n_pw, c->psi_s, false, (float*)cbuf, c->n_occ, 1.0, 0.0));
+      if (c->n_up > 0) CK(mask_cross_channel<T>((int)rows, c->n_occ, c->n_up, cbuf, c->st));
       CA(tc_product(c, (const float*)cbuf, rows, c->n_occ, c->n_occ, c->psiT_s, true, (float*)X, c->n_pw, -1.0, 1.0));
       CK(zero_pad_column<T>((int)rows, c->n_pw, X, c->st));
       return BSE_OK;
@@ -330,9 +378,54 @@ int project(bse_ctx* c, long rows, T* X, T* cbuf) {
   // cbuf [rows x n_occ] = X psi^T ; X -= cbuf psi
   CK((gemm<T, T>(false, true, (int)rows, c->n_occ, c->n_pw, 1.0, X, c->n_pw, psi, c->n_pw, 0.0,
                  cbuf, c->n_occ, 1, c->st)));
+  if (c->n_up > 0) CK(mask_cross_channel<T>((int)rows, c->n_occ, c->n_up, cbuf, c->st));
   CK((gemm<T, T>(false, false, (int)rows, c->n_pw, c->n_occ, -1.0, cbuf, c->n_occ, psi, c->n_pw,
                  1.0, X, c->n_pw, 1, c->st)));
   CK(zero_pad_column<T>((int)rows, c->n_pw, X, c->st));
+  return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// explicit QP terms of D (Eq. ham): R += sum_c psi_c delta_c <psi_c|A>, c = n_occ+1..N_QP,
+// on `rows` packed orbital rows; cbuf holds rows x n_qc coefficients
+// ---------------------------------------------------------------------------------
+template <typename T> const T* qpsi_of(bse_ctx* c);
+template <> const double* qpsi_of<double>(bse_ctx* c) { return c->qpsi64; }
+template <> const float* qpsi_of<float>(bse_ctx* c) { return c->qpsi32; }
+
+template <typename T>
+int qp_correction(bse_ctx* c, long rows, const T* A, T* R, T* cbuf, bool allow_tc = true) {
+  if (c->n_qc == 0 || rows <= 0) return BSE_OK;
+  if constexpr (sizeof(T) == 4) {
+    if (c->tc_ok && allow_tc) {
+      CA(tc_product(c, (const float*)A, rows, c->n_pw, c->n_pw, c->qpsi_s, false, (float*)cbuf, c->n_qc, 1.0, 0.0));
+      CK(scale_columns<T>((int)rows, c->n_qc, cbuf, c->n_qc, c->qdelta, c->st));
+      CA(tc_product(c, (const float*)cbuf, rows, c->n_qc, c->n_qc, c->qpsiT_s, true, (float*)R, c->n_pw, 1.0, 1.0));
+      return BSE_OK;
+    }
+  }
+  const T* q = qpsi_of<T>(c);
+  CK((gemm<T, T>(false, true, (int)rows, c->n_qc, c->n_pw, 1.0, A, c->n_pw, q, c->n_pw, 0.0, cbuf, c->n_qc, 1,
+                 c->st)));
+  CK(scale_columns<T>((int)rows, c->n_qc, cbuf, c->n_qc, c->qdelta, c->st));
+  CK((gemm<T, T>(false, false, (int)rows, c->n_pw, c->n_qc, 1.0, cbuf, c->n_qc, q, c->n_pw, 1.0, R, c->n_pw, 1,
+                 c->st)));
+  return BSE_OK;
+}
+
+// - sum_{w != v} E_vw a_sw for every vector s of a block (the occupied energies of Eq. d in a
+// rotated frame, Eq. wannier)
+template <typename T> const T* eoff_of(bse_ctx* c);
+template <> const double* eoff_of<double>(bse_ctx* c) { return c->eoff64; }
+template <> const float* eoff_of<float>(bse_ctx* c) { return c->eoff32; }
+
+template <typename T>
+int emat_term(bse_ctx* c, long n_vec, const T* A, T* R) {
+  if (!c->has_emat) return BSE_OK;
+  const long blk = (long)c->n_occ * c->n_pw;
+  for (long s = 0; s < n_vec; ++s)
+    CK((gemm<T, T>(false, false, c->n_occ, c->n_pw, c->n_occ, -1.0, eoff_of<T>(c), c->n_occ, A + s * blk, c->n_pw,
+                   1.0, R + s * blk, c->n_pw, 1, c->st)));
   return BSE_OK;
 }
 
@@ -355,42 +448,69 @@ int ensure_workspace(bse_ctx* c, long n_vec) {
   CA(dalloc(c, &p, (size_t)ngr * c->n3)); c->ws_r = p;
   CA(dalloc(c, &p, (size_t)((want + 1) / 2) * c->n3)); c->ws_h = p;
   T* q;
-  CA(dalloc(c, &q, (size_t)nf * c->n_occ)); c->ws_c = q;
+  CA(dalloc(c, &q, (size_t)nf * std::max(c->n_occ, c->n_qc))); c->ws_c = q;
   c->ws_vecs = want;
   return BSE_OK;
 }
 
+// K1d variant for a block of nv vectors without tuning: the forced one, else the tuned one
+// for this width, else the default
+template <typename T>
+int k1d_variant_for(const bse_ctx* c, int nv) {
+  if (c->k1d_force) return c->k1d_force;
+  auto it = c->k1d_var.find(nv);
+  return it != c->k1d_var.end() ? it->second : k1d_default_variant<T>(c->n_occ, nv);
+}
+
 // ---------------------------------------------------------------------------------
-// K1d tile autotuner: at the first application, time every tile variant (points and
-// vectors per CTA) that fits shared memory on the real inputs restricted to the first
-// eighth of the grid points (twice each, CUDA events on the context stream) and keep the
-// fastest. The choice only changes the tiling, never the summation order.
+// K1d tile autotuner: at the first application of a block width n_vec, time the tile
+// variants (points and vectors per CTA) that fit shared memory and pad that width least
+// (at most 3 padded vectors beyond the best), on the real inputs restricted to the first
+// eighth of the grid points (twice each, CUDA events on the context stream), and keep the
+// fastest for that width. The choice only changes the tiling, never the summation order.
 // ---------------------------------------------------------------------------------
+// Tuning results are shared by every context of the process with the same shape (precision,
+// grid, orbital count, row-block entries, block width): a later context of the same system
+// starts with the tuned variants.
+std::mutex g_k1d_tune_mu;
+std::map<std::tuple<int, long, int, long, int>, int> g_k1d_tuned;
+
 template <typename T>
 int autotune_k1d(bse_ctx* c, int nv, long n3, const T* ga, const T* gh, T* gr, double sf) {
-  if (!c->autotune) { c->k1d_sc = k1d_default_variant<T>(c->n_occ); return BSE_OK; }
+  if (!c->autotune) { c->k1d_var[nv] = k1d_default_variant<T>(c->n_occ, nv); return BSE_OK; }
+  const auto key = std::make_tuple((int)sizeof(T), n3, c->n_occ, (long)c->n_ent, nv);
+  {
+    std::lock_guard<std::mutex> lk(g_k1d_tune_mu);
+    auto it = g_k1d_tuned.find(key);
+    if (it != g_k1d_tuned.end()) { c->k1d_var[nv] = it->second; return BSE_OK; }
+  }
   const long n_pts = std::max<long>(TAU_TB, (n3 / 8) / TAU_TB * TAU_TB);
+  int least = 1 << 30;
+  for (int v = 1; v <= k1d_num_variants(); ++v)
+    if (k1d_fits<T>(c->n_occ, v)) least = std::min(least, k1d_padded_vectors(nv, v));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_sc = 0;
-  for (int sc = 1; sc <= k1d_num_variants(); ++sc) {
-    if (!k1d_fits<T>(c->n_occ, sc)) continue;
+  int best_v = 0;
+  for (int v = 1; v <= k1d_num_variants(); ++v) {
+    if (!k1d_fits<T>(c->n_occ, v) || k1d_padded_vectors(nv, v) > least + 3) continue;
     float t = 0;
     for (int rep = 0; rep < 2; ++rep) {
       CK(cudaEventRecord(e0, c->st));
       CK(k1d_tiled<T>(nv, c->n_occ, n3, ga, (const T*)c->tau, c->n_ent, c->bptr, c->bw, c->n_rblocks,
-                      vloc_of<T>(c), gh, upsi_of<T>(c), sf, gr, sc, c->st, n_pts));
+                      vloc_of<T>(c), gh, upsi_of<T>(c), sf, gr, v, c->st, n_pts));
       CK(cudaEventRecord(e1, c->st));
       CK(cudaEventSynchronize(e1));
       CK(cudaEventElapsedTime(&t, e0, e1));
     }
-    if (t < best) { best = t; best_sc = sc; }
+    if (t < best) { best = t; best_v = v; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c->k1d_sc = best_sc ? best_sc : k1d_default_variant<T>(c->n_occ);
+  c->k1d_var[nv] = best_v ? best_v : k1d_default_variant<T>(c->n_occ, nv);
+  std::lock_guard<std::mutex> lk(g_k1d_tune_mu);
+  g_k1d_tuned[key] = c->k1d_var[nv];
   return BSE_OK;
 }
 
@@ -405,7 +525,7 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
   const int N = c->N;
   const long n3 = c->n3;
   const T* tau = (const T*)c->tau;
-  const double sf = (c->spin == 0) ? 2.0 : 0.0;
+  const double sf = c->k1e_factor();
   for (long s0 = 0; s0 < n_vec; s0 += chunk) {
     const long nv = std::min(chunk, n_vec - s0);
     const long nf = nv * c->n_occ;
@@ -444,10 +564,11 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
                ((double)c->n_pairs + 2.0 * nf + 1.0 + nv + c->n_occ) * n3 * sz,
                (2.0 * nnz * nv + 5.0 * nf) * n3);
       if (c->tau_entry) {
-        if (c->k1d_sc == 0) CA(autotune_k1d<T>(c, (int)nv, n3, (const T*)ga, (const T*)gh, (T*)gr, sf));
-        CK(k1d_tiled<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->n_ent, c->bptr, c->bw,
-                        c->n_rblocks, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr,
-                        c->k1d_sc, c->st));
+        if (!c->k1d_force && !c->k1d_var.count((int)nv))
+          CA(autotune_k1d<T>(c, (int)nv, n3, (const T*)ga, (const T*)gh, (T*)gr, sf));
+        CK(k1d_tiled<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->n_ent, c->bptr, c->bw, c->n_rblocks,
+                        vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, k1d_variant_for<T>(c, (int)nv),
+                        c->st));
       } else {
         CK(k1d_combine<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->n_pairs, c->nbr_ptr, c->nbr_w, c->nbr_p,
                           vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
@@ -462,6 +583,15 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
       CK(grid_to_sphere<T>(gr, nf, c->n_pw, c->n_half, N, c->sph, tw_of<T>(c), ga, 1.0 / (double)n3, aout,
                            ain, g2h_of<T>(c), esh_of<T>(c), c->n_occ, c->st));
     }
+    if (c->n_qc > 0) {
+      Scope sc(c, "qp_terms", (3.0 * nf * c->n_pw + (double)c->n_qc * c->n_pw) * sz,
+               4.0 * nf * c->n_qc * (double)c->n_pw);
+      CA(qp_correction<T>(c, nf, ain, aout, (T*)c->ws_c));
+    }
+    if (c->has_emat) {
+      Scope sc(c, "occupied_energy_matrix", 3.0 * nf * c->n_pw * sz, 2.0 * nf * c->n_occ * (double)c->n_pw);
+      CA(emat_term<T>(c, nv, ain, aout));
+    }
     {
       Scope sc(c, "projector_pc", (3.0 * nf * c->n_pw + (double)c->n_occ * c->n_pw) * sz,
                4.0 * nf * c->n_occ * (double)c->n_pw);
@@ -474,6 +604,9 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
 // ---------------------------------------------------------------------------------
 // overlaps, pair rule and screened integrals (Eqs. overlap, tau, tau_from_tau_u, pdep)
 // ---------------------------------------------------------------------------------
+// contexts inside build_tau at this moment (process-wide)
+std::atomic<int> g_tau_builders{0};
+
 template <typename T>
 int build_tau_impl(bse_ctx* c) {
   const long n3 = c->n3;
@@ -497,13 +630,19 @@ int build_tau_impl(bse_ctx* c) {
     dfree(c, rho_hi); dfree(c, rho_lo); dfree(c, gram); dfree(c, dg);
   }
   if (!all_finite(c->O_h.data(), (long)n * n)) return fail(c, BSE_ERR_NUMERIC, "non-finite overlap");
-  c->thr = choose_threshold(c->O_h, n, c->thr_in, c->keep_pairs);
+  // the screened direct term conserves spin: pairs across the channels of a spin-polarised
+  // system are never kept and take no part in the threshold rule (overlap -1, below [0, 1])
+  std::vector<double> O_rule = c->O_h;
+  for (int v = 0; v < n; ++v)
+    for (int w = 0; w < n; ++w)
+      if (c->chan(v) != c->chan(w)) O_rule[(size_t)v * n + w] = -1.0;
+  c->thr = choose_threshold(O_rule, n, c->thr_in, c->keep_pairs);
   // pair list v <= w (row-major) and CSR neighbour lists in both directions
   std::vector<std::vector<int>> pid(n, std::vector<int>(n, -1));
   c->pv_h.clear(); c->pw_h.clear();
   for (int v = 0; v < n; ++v)
     for (int w = v; w < n; ++w) {
-      const bool keep = (v == w) || (c->O_h[(size_t)v * n + w] >= c->thr);
+      const bool keep = (v == w) || (O_rule[(size_t)v * n + w] >= c->thr);
       if (keep) {
         pid[v][w] = pid[w][v] = (int)c->pv_h.size();
         c->pv_h.push_back(v); c->pw_h.push_back(w);
@@ -574,15 +713,18 @@ int build_tau_impl(bse_ctx* c) {
   // about 2.8 times the per-pair values, so it is used only while it takes at most half of
   // the free device memory (large FP64 systems keep the per-pair layout);
   // BSE_TAU_LAYOUT=pair forces the per-pair layout and the untiled kernel.
+  // Contexts that build tau at the same time (bse_solve_batch) share the free memory: each
+  // takes at most its share of the half.
   T* tau;
   {
     size_t fr = 0, tot = 0;
-    cudaMemGetInfo(&fr, &tot);
+    CK(cudaMemGetInfo(&fr, &tot));
     const double t4 = (double)c->n_ent * 4.0 * (double)n3 * sizeof(T);
     const char* lay = getenv("BSE_TAU_LAYOUT");
     const bool force_pair = lay && std::strcmp(lay, "pair") == 0;
-    c->tau_entry = !force_pair && k1d_default_variant<T>(c->n_occ) > 0 && n3 % TAU_TB == 0 &&
-                   t4 <= 0.5 * (double)fr;
+    const int builders = std::max(1, g_tau_builders.load());
+    c->tau_entry = !force_pair && k1d_default_variant<T>(c->n_occ, 1) > 0 && n3 % TAU_TB == 0 &&
+                   t4 <= 0.5 * (double)fr / builders;
   }
   if (c->tau_entry) {
     CA(dalloc(c, &tau, (size_t)c->n_ent * 4 * n3));
@@ -766,7 +908,7 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
     // margin beyond rounding, or at the pad coordinate, is rejected without device work.
     {
       const int jc = (int)(top.first.flat % c->n_pw);
-      if (jc == 1 || 1.0 - c->occw_h[jc] < 0.01 * (1.0 - 1e-3)) continue;
+      if (jc == 1 || 1.0 - c->occw_h[(size_t)c->chan(v) * c->n_pw + jc] < 0.01 * (1.0 - 1e-3)) continue;
     }
     T* x = V + (long)m * dim;
     CK(set_unit<T>(x, dim, top.first.flat, c->st));
@@ -975,6 +1117,214 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
   return BSE_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// Lanczos chains for the absorption spectrum (Section 4: N_Lanczos applications of the
+// operator per polarisation direction). All directions run together as one block; the
+// three-term recursion stays on the device, so the chain needs no host round trip.
+// ---------------------------------------------------------------------------------
+template <typename T>
+int lanczos_impl(bse_ctx* c, int np, const int* dirs, int m, double* alpha_h, double* beta_h, double* norm2_h) {
+  const long dim = (long)c->n_occ * c->n_pw;
+  std::vector<void*> mine;
+  auto al = [&](auto** p, size_t n) {
+    int r = dalloc(c, p, n);
+    if (r == BSE_OK) mine.push_back(*p);
+    return r;
+  };
+  struct Guard {
+    bse_ctx* c; std::vector<void*>* m;
+    ~Guard() { for (void* p : *m) dfree(c, p); }
+  } guard{c, &mine};
+  T *Q, *Qp, *W, *pcbuf;
+  double *gd, *n2, *C, *alpha, *beta, *b0;
+  CA(al(&Q, (size_t)np * dim)); CA(al(&Qp, (size_t)np * dim)); CA(al(&W, (size_t)np * dim));
+  CA(al(&pcbuf, (size_t)np * c->n_occ * c->n_occ + 16));
+  CA(al(&gd, (size_t)np * c->n_pw)); CA(al(&n2, (size_t)np)); CA(al(&C, (size_t)np * np));
+  CA(al(&alpha, (size_t)np * m)); CA(al(&beta, (size_t)np * m)); CA(al(&b0, (size_t)np));
+  std::vector<double> gh((size_t)np * c->n_pw);
+  for (int p = 0; p < np; ++p)
+    std::copy(c->gcart_h.begin() + (size_t)dirs[p] * c->n_pw, c->gcart_h.begin() + (size_t)(dirs[p] + 1) * c->n_pw,
+              gh.begin() + (size_t)p * c->n_pw);
+  CK(cudaMemcpyAsync(gd, gh.data(), sizeof(double) * gh.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemsetAsync(alpha, 0, sizeof(double) * np * m, c->st));
+  CK(cudaMemsetAsync(beta, 0, sizeof(double) * np * m, c->st));
+  // start block d = P_c(-d psi / d r_i), then q_1 = d / |d|
+  for (int p = 0; p < np; ++p) CK(dipole_rhs<T>(c->n_occ, c->n_pw, c->psi64, gd + (size_t)p * c->n_pw, W + p * dim, c->st));
+  CA(project<T>(c, (long)np * c->n_occ, W, pcbuf));
+  CK(row_norms2<T>(np, dim, W, n2, c->st));
+  CK(cudaMemcpyAsync(norm2_h, n2, sizeof(double) * np, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (int p = 0; p < np; ++p)
+    if (!(norm2_h[p] > 0) || !std::isfinite(norm2_h[p]))
+      return fail(c, BSE_ERR_NUMERIC, "the dipole start vector vanishes in the conduction space");
+  CK(lanczos_normalize<T>(np, dim, W, n2, Q, b0, 1, c->st));
+  CK(cudaMemsetAsync(Qp, 0, sizeof(T) * np * dim, c->st));
+  for (int k = 0; k < m; ++k) {
+    CA(apply_impl<T>(c, np, Q, W));                                              // w = L q_k
+    if (k > 0) CK(lanczos_axpy<T>(np, dim, W, Qp, beta + k, m, nullptr, 0, c->st));   // - beta_k q_{k-1}
+    {
+      Scope sc(c, "lanczos_recursion", 4.0 * np * (double)dim * sizeof(T), 6.0 * np * (double)dim);
+      CK(tn_product<T>(c, np, np, dim, Q, dim, W, dim, C, np));                 // alpha_k = <q_k|w>
+      CK(lanczos_axpy<T>(np, dim, W, Q, C, np + 1, alpha + k, m, c->st));       // w -= alpha_k q_k
+      if (k + 1 < m) {
+        // back onto the conduction space: rounding components in the occupied space (where L
+        // is zero) would grow exponentially under the three-term recurrence
+        CA(project<T>(c, (long)np * c->n_occ, W, pcbuf));
+        CK(row_norms2<T>(np, dim, W, n2, c->st));                               // beta_{k+1} = |w|
+        std::swap(Q, Qp);
+        CK(lanczos_normalize<T>(np, dim, W, n2, Q, beta + k + 1, m, c->st));    // q_{k+1} = w / beta
+      }
+    }
+  }
+  CK(cudaMemcpyAsync(alpha_h, alpha, sizeof(double) * np * m, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(beta_h, beta, sizeof(double) * np * m, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (!all_finite(alpha_h, (long)np * m) || !all_finite(beta_h, (long)np * m))
+    return fail(c, BSE_ERR_NUMERIC, "non-finite Lanczos coefficient");
+  return BSE_OK;
+}
+
+int spectrum_impl(bse_ctx* c, int m, const double* alpha_h, const double* beta_h, double norm2, int n_omega,
+                  const double* omega_h, double eta, double* gre_h, double* gim_h) {
+  double *a, *b, *om, *gr, *gi;
+  CA(dalloc(c, &a, (size_t)m)); CA(dalloc(c, &b, (size_t)m)); CA(dalloc(c, &om, (size_t)n_omega));
+  CA(dalloc(c, &gr, (size_t)n_omega)); CA(dalloc(c, &gi, (size_t)n_omega));
+  struct G8 { bse_ctx* c; std::vector<void*> v; ~G8() { for (void* x : v) dfree(c, x); } } g8{c, {a, b, om, gr, gi}};
+  CK(cudaMemcpyAsync(a, alpha_h, sizeof(double) * m, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(b, beta_h, sizeof(double) * m, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(om, omega_h, sizeof(double) * n_omega, cudaMemcpyHostToDevice, c->st));
+  CK(continued_fraction(m, a, b, norm2, n_omega, om, eta, gr, gi, c->st));
+  CK(cudaMemcpyAsync(gre_h, gr, sizeof(double) * n_omega, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(gim_h, gi, sizeof(double) * n_omega, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Wannier localisation (Section 2, Eqs. wannier and spread): JADE on the six matrices
+// A^(n) = <psi|M^(n)|psi>, then the context's orbitals become psi~ = U^T psi and the
+// occupied energies the matrix U^T diag(eps) U
+// ---------------------------------------------------------------------------------
+// recompute everything derived from psi64: psi on the grid, the FP32 copies and the BF16
+// splits of the mixed path
+int refresh_orbitals(bse_ctx* c) {
+  const long ng = (c->n_occ + 1) / 2, npsi = (long)c->n_occ * c->n_pw;
+  CK((sphere_unpack<double, double>(c->psi64, c->n_occ, c->n_pw, c->n_half, c->gpos, c->gneg, (double2*)c->upsi64,
+                                    c->n3, true, false, c->st)));
+  CK(fft3d<double>((double2*)c->upsi64, ng, c->N, +1, c->tw64, c->st));
+  if (c->prec == BSE_PREC_MIXED) {
+    CK((convert<double, float>(ng * 2 * c->n3, c->upsi64, c->upsi32, c->st)));
+    CK((convert<double, float>(npsi, c->psi64, c->psi32, c->st)));
+    if (c->tc_ok) {
+      CK(bf16_split64(c->psi64, c->n_occ, c->n_pw, c->n_pw, c->psi_s.hi, c->psi_s.lo, c->psi_s.ld, false, c->st));
+      CK(bf16_split64(c->psi64, c->n_occ, c->n_pw, c->n_pw, c->psiT_s.hi, c->psiT_s.lo, c->psiT_s.ld, true, c->st));
+    }
+  }
+  return BSE_OK;
+}
+
+int localize_impl(bse_ctx* c, int max_sweeps, double tol, double* U_out) {
+  const int n = c->n_occ;
+  const long n3 = c->n3;
+  constexpr int K = 6;
+  std::vector<void*> mine;
+  auto al = [&](auto** p, size_t m) {
+    int r = dalloc(c, p, m);
+    if (r == BSE_OK) mine.push_back(*p);
+    return r;
+  };
+  struct Guard {
+    bse_ctx* c; std::vector<void*>* m;
+    ~Guard() { for (void* p : *m) dfree(c, p); }
+  } guard{c, &mine};
+  double *u, *W, *A, *U, *Bd, *tmp;
+  double2* cs;
+  int2* pairs_d;
+  unsigned* smax;
+  CA(al(&u, (size_t)n * n3)); CA(al(&W, (size_t)n * n3)); CA(al(&A, (size_t)K * n * n));
+  CA(al(&U, (size_t)n * n)); CA(al(&Bd, (size_t)K * n)); CA(al(&tmp, (size_t)n * c->n_pw));
+  // A^(n) = N^-3 u M u^T and the diagonals of B^(n) (u = Omega^{1/2} psi on the grid; the
+  // products are band-limited, so the grid sums are exact)
+  CK(pair_grid_to_rows<double>(n, c->upsi64, n3, u, c->st));
+  const double w = 1.0 / (double)n3;
+  for (int op = 0; op < K; ++op) {
+    CK(jade_weight(n, n3, c->N, op, u, W, false, c->st));
+    CK((gemm<double, double>(false, true, n, n, (int)n3, w, u, n3, W, n3, 0.0, A + (size_t)op * n * n, n, 0, c->st)));
+    CK(jade_weight(n, n3, c->N, op, u, W, true, c->st));
+    CK(row_dots(n, n3, u, W, Bd + (size_t)op * n, c->st));
+  }
+  auto spread_now = [&](double& out) -> int {
+    std::vector<double> hA((size_t)K * n * n), hB((size_t)K * n);
+    CK(cudaMemcpyAsync(hA.data(), A, sizeof(double) * hA.size(), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(hB.data(), Bd, sizeof(double) * hB.size(), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    double sg = 0;
+    for (int op = 0; op < K; ++op)
+      for (int v = 0; v < n; ++v) {
+        const double d = hA[(size_t)op * n * n + (size_t)v * n + v];
+        sg += w * hB[(size_t)op * n + v] - d * d;
+      }
+    out = sg;
+    return BSE_OK;
+  };
+  CA(spread_now(c->spread0));
+  // sweeps: first on A^(1) alone (its eigenvectors start U, as in the paper), then on all six
+  std::vector<int2> sched;
+  int rounds = 0, per = 0;
+  jade_schedule(n, sched, rounds, per);
+  CA(al(&pairs_d, sched.size())); CA(al(&cs, (size_t)per)); CA(al(&smax, 1));
+  CK(cudaMemcpyAsync(pairs_d, sched.data(), sizeof(int2) * sched.size(), cudaMemcpyHostToDevice, c->st));
+  CK(set_identity(n, U, c->st));
+  for (int stage = 0; stage < 2; ++stage) {
+    const int k_use = stage == 0 ? 1 : K;
+    for (int sw = 0; sw < max_sweeps; ++sw) {
+      CK(cudaMemsetAsync(smax, 0, sizeof(unsigned), c->st));
+      for (int r = 0; r < rounds; ++r)
+        CK(jade_round(k_use, K, n, A, U, pairs_d + (size_t)r * per, per, cs, smax, c->st));
+      unsigned hs = 0;
+      CK(cudaMemcpyAsync(&hs, smax, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      float f;
+      std::memcpy(&f, &hs, sizeof(f));
+      if (!std::isfinite(f)) return fail(c, BSE_ERR_NUMERIC, "non-finite rotation in the localisation");
+      if ((double)f <= tol) break;
+    }
+  }
+  CA(spread_now(c->spread1));
+  // psi~ = U^T psi; E = U^T diag(eps) U (diagonal -> eps, the rest -> the operator term)
+  CK((gemm<double, double>(true, false, n, c->n_pw, n, 1.0, U, n, c->psi64, c->n_pw, 0.0, tmp, c->n_pw, 1, c->st)));
+  CK(cudaMemcpyAsync(c->psi64, tmp, sizeof(double) * n * c->n_pw, cudaMemcpyDeviceToDevice, c->st));
+  CA(refresh_orbitals(c));
+  double *Ev, *E;
+  CA(al(&Ev, (size_t)n)); CA(al(&E, (size_t)n * n));
+  CK(cudaMemcpyAsync(Ev, c->eps_h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(W, U, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, c->st));
+  CK(scale_rows<double>(n, n, W, Ev, c->st));                                   // diag(eps) U
+  CK((gemm<double, double>(true, false, n, n, n, 1.0, U, n, W, n, 0.0, E, n, 1, c->st)));
+  std::vector<double> hE((size_t)n * n), hU((size_t)n * n);
+  CK(cudaMemcpyAsync(hE.data(), E, sizeof(double) * hE.size(), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(hU.data(), U, sizeof(double) * hU.size(), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (!all_finite(hE.data(), (long)n * n) || !all_finite(hU.data(), (long)n * n))
+    return fail(c, BSE_ERR_NUMERIC, "non-finite localising rotation");
+  std::vector<double> ediag(n), esh(n);
+  for (int v = 0; v < n; ++v) { ediag[v] = hE[(size_t)v * n + v]; hE[(size_t)v * n + v] = 0.0; }
+  c->eps_h = ediag;
+  for (int v = 0; v < n; ++v) esh[v] = c->scissor - ediag[v];
+  std::vector<float> eshf(esh.begin(), esh.end()), ef(hE.begin(), hE.end());
+  CK(cudaMemcpyAsync(c->eps, ediag.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->esh64, esh.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->esh32, eshf.data(), sizeof(float) * n, cudaMemcpyHostToDevice, c->st));
+  if (!c->eoff64) CA(dalloc(c, &c->eoff64, (size_t)n * n));
+  if (!c->eoff32) CA(dalloc(c, &c->eoff32, (size_t)n * n));
+  CK(cudaMemcpyAsync(c->eoff64, hE.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->eoff32, ef.data(), sizeof(float) * n * n, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->has_emat = true;
+  if (U_out) std::memcpy(U_out, hU.data(), sizeof(double) * n * n);
+  return BSE_OK;
+}
+
 }  // namespace
 
 // =================================================================================
@@ -990,30 +1340,40 @@ const char* bse_last_error(const bse_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 void bse_destroy(bse_ctx* ctx) {
   if (!ctx) return;
-  for (void* p : ctx->allocs) cudaFreeAsync(p, ctx->st);
+  for (void* p : ctx->allocs) dfree_raw(ctx, p);
   ctx->allocs.clear();
   cudaStreamSynchronize(ctx->st);
   delete ctx;
 }
 
-int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) {
+int bse_create(const bse_system* s, int precision, bse_alloc_fn alloc_fn, bse_free_fn free_fn, void* user,
+               void* stream, bse_ctx** out) {
   if (!out) return BSE_ERR_INVALID_ARG;
   *out = nullptr;
   if (!s) return BSE_ERR_INVALID_ARG;
   if (precision != BSE_PREC_FP64 && precision != BSE_PREC_MIXED) return BSE_ERR_INVALID_ARG;
+  if ((alloc_fn == nullptr) != (free_fn == nullptr)) return BSE_ERR_INVALID_ARG;
   bse_ctx* c = new bse_ctx();
   auto bail = [&](int code) { if (code != BSE_OK) { *out = c; } return code; };
   c->st = (cudaStream_t)stream;
+  c->ua = alloc_fn;
+  c->uf = free_fn;
+  c->uu = user;
   c->prec = precision;
   if (!fft_supported(s->n_grid)) return bail(fail(c, BSE_ERR_INVALID_ARG, "n_grid must be one of 16, 32, 48, 64, 72, 96"));
   if (!(s->L > 0) || s->n_half < 1 || s->n_occ < 1 || s->n_pdep < 0 || !s->miller || !s->psi ||
-      !s->eps || !s->v_loc || (s->n_pdep > 0 && (!s->pdep || !s->lambda)) || (s->spin != 0 && s->spin != 1))
+      (!s->eps && s->n_qp == 0) || !s->v_loc || (s->n_pdep > 0 && (!s->pdep || !s->lambda)) ||
+      (s->spin != 0 && s->spin != 1))
     return bail(fail(c, BSE_ERR_INVALID_ARG, "invalid system sizes or null pointers"));
+  if (s->n_qp != 0 && (s->n_qp <= s->n_occ || !s->qp_psi || !s->qp_eps_ks || !s->qp_eps))
+    return bail(fail(c, BSE_ERR_INVALID_ARG, "n_qp must be 0 or > n_occ, with qp_psi, qp_eps_ks and qp_eps"));
   if (s->overlap_thr <= 0 && s->keep_pairs < 1)
     return bail(fail(c, BSE_ERR_INVALID_ARG, "need overlap_thr > 0 or keep_pairs >= 1"));
   c->N = s->n_grid; c->n3 = (long)c->N * c->N * c->N; c->L = s->L; c->omega = s->L * s->L * s->L;
   c->n_half = s->n_half; c->n_pw = 2 * s->n_half; c->n_occ = s->n_occ; c->n_pdep = s->n_pdep;
   c->spin = s->spin; c->scissor = s->scissor; c->thr_in = s->overlap_thr; c->keep_pairs = s->keep_pairs;
+  if (s->n_up < 0 || s->n_up > s->n_occ) return bail(fail(c, BSE_ERR_INVALID_ARG, "n_up must be in [0, n_occ]"));
+  c->n_up = s->n_up;
   if (c->n_occ >= c->n_pw - 1) return bail(fail(c, BSE_ERR_INVALID_ARG, "n_occ must be smaller than the sphere dimension"));
   const int rmax = (c->N - 1) / 4;
   std::vector<int> gpos(c->n_half), gneg(c->n_half);
@@ -1032,10 +1392,29 @@ int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) 
     gneg[k] = idx(-m[0], -m[1], -m[2]);
   }
   const long npsi = (long)c->n_occ * c->n_pw;
-  if (!all_finite(s->psi, npsi) || !all_finite(s->eps, c->n_occ) || !all_finite(s->v_loc, c->n3) ||
-      !std::isfinite(s->scissor) || (c->n_pdep > 0 && (!all_finite(s->pdep, (long)c->n_pdep * c->n_pw) ||
-                                                       !all_finite(s->lambda, c->n_pdep))))
+  c->n_qc = s->n_qp ? s->n_qp - s->n_occ : 0;
+  if (!all_finite(s->psi, npsi) || (s->n_qp == 0 && (!all_finite(s->eps, c->n_occ) || !std::isfinite(s->scissor))) ||
+      !all_finite(s->v_loc, c->n3) ||
+      (c->n_pdep > 0 && (!all_finite(s->pdep, (long)c->n_pdep * c->n_pw) || !all_finite(s->lambda, c->n_pdep))) ||
+      (c->n_qc > 0 && (!all_finite(s->qp_psi, (long)c->n_qc * c->n_pw) || !all_finite(s->qp_eps_ks, s->n_qp) ||
+                       !all_finite(s->qp_eps, s->n_qp))))
     return bail(fail(c, BSE_ERR_NUMERIC, "non-finite input"));
+  for (int q = 0; q < c->n_qc; ++q)
+    if (s->qp_psi[(long)q * c->n_pw + 1] != 0.0) return bail(fail(c, BSE_ERR_INVALID_ARG, "qp_psi pad entry (index 1) must be 0"));
+  // D of Eq. (d) with the QP Hamiltonian of Eq. (ham): occupied energies eps^QP_v, the uniform
+  // shift Delta (the scissor, or the average of the QP corrections over N_mid..N_QP) and, with
+  // explicit QP data, the corrections delta_c of the conduction states n_occ+1..N_QP
+  std::vector<double> eps_use(c->n_occ), qdelta_h(std::max(1, c->n_qc), 0.0);
+  if (c->n_qc > 0) {
+    const int nqp = s->n_qp, n_mid = (s->n_occ + s->n_qp) / 2;
+    double sum = 0;
+    for (int n = n_mid - 1; n < nqp; ++n) sum += s->qp_eps[n] - s->qp_eps_ks[n];
+    c->scissor = sum / (double)(nqp - n_mid + 1);
+    for (int v = 0; v < c->n_occ; ++v) eps_use[v] = s->qp_eps[v];
+    for (int q = 0; q < c->n_qc; ++q) qdelta_h[q] = s->qp_eps[c->n_occ + q] - s->qp_eps_ks[c->n_occ + q] - c->scissor;
+  } else {
+    for (int v = 0; v < c->n_occ; ++v) eps_use[v] = s->eps[v];
+  }
   for (int v = 0; v < c->n_occ; ++v)
     if (s->psi[(long)v * c->n_pw + 1] != 0.0) return bail(fail(c, BSE_ERR_INVALID_ARG, "psi pad entry (index 1) must be 0"));
   for (int a = 0; a < c->n_pdep; ++a) {
@@ -1046,13 +1425,16 @@ int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) 
   // host tables
   const double g = 2.0 * M_PI / c->L;
   c->g2p_h.assign(c->n_pw, 0.0);
+  c->gcart_h.assign((size_t)3 * c->n_pw, 0.0);
   for (int k = 0; k < c->n_half; ++k) {
     const int* m = &s->miller[3 * k];
     const double g2 = g * g * (double)(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
     c->g2p_h[2 * k] = g2;
     c->g2p_h[2 * k + 1] = (k == 0) ? 0.0 : g2;
+    for (int a = 0; a < 3; ++a) c->gcart_h[(size_t)a * c->n_pw + 2 * k] = c->gcart_h[(size_t)a * c->n_pw + 2 * k + 1] =
+        (k == 0) ? 0.0 : g * (double)m[a];
   }
-  c->eps_h.assign(s->eps, s->eps + c->n_occ);
+  c->eps_h = eps_use;
   double vs = 0;
   for (long r = 0; r < c->n3; ++r) vs += s->v_loc[r];
   c->v0 = vs / (double)c->n3;
@@ -1065,11 +1447,12 @@ int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) 
     size_t bud = std::min<size_t>((size_t)64 << 30, (size_t)(0.4 * (double)fr));
     if (const char* e = getenv("BSE_WORKSPACE_GB")) bud = (size_t)(atof(e) * (double)(1ull << 30));
     if (const char* e = getenv("BSE_AUTOTUNE")) c->autotune = atoi(e) != 0;
+    if (const char* e = getenv("BSE_TC_WAIT_LIMIT")) c->tc_wait_limit = atoll(e);
     // BSE_K1D_VARIANT=v fixes the K1d tile variant (no autotuning); ignored if it does not fit
     if (const char* e = getenv("BSE_K1D_VARIANT")) {
       const int v = atoi(e);
       const bool ok = (precision == BSE_PREC_FP64) ? k1d_fits<double>(s->n_occ, v) : k1d_fits<float>(s->n_occ, v);
-      if (ok) c->k1d_sc = v;
+      if (ok) c->k1d_force = v;
     }
     c->ws_budget = std::max<size_t>(bud, 1);
   }
@@ -1101,11 +1484,15 @@ int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) 
     c->sph = SphereMap{h.NS, h.NC, h.NX, fp, fn, zs, jc, cs, cy, cx, xs, xc};
   }
   UPLOAD(c->g2p, c->g2p_h.data(), c->n_pw);
-  UPLOAD(c->eps, s->eps, c->n_occ);
+  UPLOAD(c->eps, eps_use.data(), c->n_occ);
+  if (c->n_qc > 0) {
+    UPLOAD(c->qpsi64, s->qp_psi, (long)c->n_qc * c->n_pw);
+    UPLOAD(c->qdelta, qdelta_h.data(), c->n_qc);
+  }
   {
     std::vector<double> g2h(c->n_pw), esh(c->n_occ);
     for (int j = 0; j < c->n_pw; ++j) g2h[j] = 0.5 * c->g2p_h[j];
-    for (int v = 0; v < c->n_occ; ++v) esh[v] = c->scissor - s->eps[v];
+    for (int v = 0; v < c->n_occ; ++v) esh[v] = c->scissor - eps_use[v];
     std::vector<float> g2hf(g2h.begin(), g2h.end()), eshf(esh.begin(), esh.end());
     UPLOAD(c->g2h64, g2h.data(), g2h.size());
     UPLOAD(c->esh64, esh.data(), esh.size());
@@ -1114,9 +1501,10 @@ int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) 
   }
   UPLOAD(c->f, fh.data(), fh.size());
   UPLOAD(c->psi64, s->psi, npsi);
-  c->occw_h.assign(c->n_pw, 0.0);
+  c->occw_h.assign((size_t)2 * c->n_pw, 0.0);
   for (int v = 0; v < c->n_occ; ++v)
-    for (int j = 0; j < c->n_pw; ++j) c->occw_h[j] += s->psi[(long)v * c->n_pw + j] * s->psi[(long)v * c->n_pw + j];
+    for (int j = 0; j < c->n_pw; ++j)
+      c->occw_h[(size_t)c->chan(v) * c->n_pw + j] += s->psi[(long)v * c->n_pw + j] * s->psi[(long)v * c->n_pw + j];
   UPLOAD(c->vloc64, s->v_loc, c->n3);
   if (c->n_pdep > 0) UPLOAD(c->pdep64, s->pdep, (long)c->n_pdep * c->n_pw);
   std::vector<double2> tw;
@@ -1152,6 +1540,10 @@ int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) 
         if ((r = dalloc(c, &c->pdep32, (size_t)c->n_pdep * c->n_pw)) != BSE_OK) return bail(r);
         e = convert<double, float>((long)c->n_pdep * c->n_pw, c->pdep64, c->pdep32, c->st);
       }
+      if (e == cudaSuccess && c->n_qc > 0) {
+        if ((r = dalloc(c, &c->qpsi32, (size_t)c->n_qc * c->n_pw)) != BSE_OK) return bail(r);
+        e = convert<double, float>((long)c->n_qc * c->n_pw, c->qpsi64, c->qpsi32, c->st);
+      }
       if (e != cudaSuccess) return bail(cuda_fail(c, e, "FP32 copies"));
       // BF16x3 tensor-core operands: Psi, Psi^T, Phi, Phi^T split once
       if ((r = dalloc(c, &c->d_err, 1)) != BSE_OK) return bail(r);
@@ -1161,6 +1553,8 @@ int bse_create(const bse_system* s, int precision, void* stream, bse_ctx** out) 
         if (rr == BSE_OK) rr = make_split64(c, c->psiT_s, c->psi64, c->n_occ, c->n_pw, true);
         if (rr == BSE_OK && c->n_pdep > 0) rr = make_split64(c, c->pdep_s, c->pdep64, c->n_pdep, c->n_pw, false);
         if (rr == BSE_OK && c->n_pdep > 0) rr = make_split64(c, c->pdepT_s, c->pdep64, c->n_pdep, c->n_pw, true);
+        if (rr == BSE_OK && c->n_qc > 0) rr = make_split64(c, c->qpsi_s, c->qpsi64, c->n_qc, c->n_pw, false);
+        if (rr == BSE_OK && c->n_qc > 0) rr = make_split64(c, c->qpsiT_s, c->qpsi64, c->n_qc, c->n_pw, true);
         if (rr != BSE_OK) return bail(rr);
         c->tc_ok = true;
       }
@@ -1185,7 +1579,9 @@ static int check_device_flag(bse_ctx* c) {
 
 int bse_build_tau(bse_ctx* c, int64_t* n_pairs_out, double* thr_out) {
   if (!c) return BSE_ERR_INVALID_ARG;
+  ++g_tau_builders;
   int r = (c->prec == BSE_PREC_FP64) ? build_tau_impl<double>(c) : build_tau_impl<float>(c);
+  --g_tau_builders;
   cudaStreamSynchronize(c->st);
   c->prof.resolve();
   if (r != BSE_OK) return r;
@@ -1240,6 +1636,44 @@ int bse_davidson(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, void
     if (f != BSE_OK) return f;
   }
   return r;
+}
+
+int bse_localize(bse_ctx* c, int max_sweeps, double tol, double* U_out, double* spread_out) {
+  if (!c) return BSE_ERR_INVALID_ARG;
+  if (max_sweeps < 1 || !(tol > 0)) return fail(c, BSE_ERR_INVALID_ARG, "bse_localize: max_sweeps >= 1, tol > 0");
+  if (c->tau_ready) return fail(c, BSE_ERR_STATE, "bse_localize must run before bse_build_tau");
+  if (c->n_up > 0) return fail(c, BSE_ERR_INVALID_ARG, "bse_localize: closed-shell systems only");
+  int r = localize_impl(c, max_sweeps, tol, U_out);
+  cudaStreamSynchronize(c->st);
+  if (r != BSE_OK) return r;
+  if (spread_out) { spread_out[0] = c->spread0; spread_out[1] = c->spread1; }
+  return BSE_OK;
+}
+
+int bse_lanczos(bse_ctx* c, int n_pol, const int* dirs, int n_steps, double* alpha_out, double* beta_out,
+                double* norm2_out) {
+  if (!c) return BSE_ERR_INVALID_ARG;
+  if (n_pol < 1 || n_pol > 3 || !dirs || n_steps < 1 || !alpha_out || !beta_out || !norm2_out)
+    return fail(c, BSE_ERR_INVALID_ARG, "bse_lanczos: need 1 <= n_pol <= 3, dirs, n_steps >= 1 and outputs");
+  for (int p = 0; p < n_pol; ++p)
+    if (dirs[p] < 0 || dirs[p] > 2) return fail(c, BSE_ERR_INVALID_ARG, "bse_lanczos: directions are 0, 1, 2");
+  if (!c->tau_ready) return fail(c, BSE_ERR_STATE, "bse_build_tau must run before bse_lanczos");
+  int r = (c->prec == BSE_PREC_FP64)
+              ? lanczos_impl<double>(c, n_pol, dirs, n_steps, alpha_out, beta_out, norm2_out)
+              : lanczos_impl<float>(c, n_pol, dirs, n_steps, alpha_out, beta_out, norm2_out);
+  cudaStreamSynchronize(c->st);
+  c->prof.resolve();
+  if (r != BSE_OK) return r;
+  return check_device_flag(c);
+}
+
+int bse_lanczos_spectrum(bse_ctx* c, int n_steps, const double* alpha, const double* beta, double norm2,
+                         int n_omega, const double* omega, double eta, double* g_re, double* g_im) {
+  if (!c) return BSE_ERR_INVALID_ARG;
+  if (n_steps < 1 || !alpha || !beta || n_omega < 0 || (n_omega > 0 && (!omega || !g_re || !g_im)) || !(eta > 0))
+    return fail(c, BSE_ERR_INVALID_ARG, "bse_lanczos_spectrum: bad arguments (eta must be > 0)");
+  if (n_omega == 0) return BSE_OK;
+  return spectrum_impl(c, n_steps, alpha, beta, norm2, n_omega, omega, eta, g_re, g_im);
 }
 
 int bse_solve_batch(bse_ctx* const* ctxs, int n, const bse_davidson_opts* o, double* omega_out,
@@ -1338,11 +1772,11 @@ int lp_step(bse_ctx* c, const float* d_params, int bf, double* d_grad, double* d
   auto al = [&](auto** p, size_t n) { int r = dalloc(c, p, n); if (r == BSE_OK) tmp.push_back(*p); return r; };
   struct G2 { bse_ctx* c; std::vector<void*>* t; ~G2() { for (void* p : *t) dfree(c, p); } } guard{c, &tmp};
   float *X, *H1, *H2, *O, *DO, *DZ1, *DZ2, *ones;
-  double *Gv, *Y, *dg, *cb, *gpart, *ab, *bb;
+  double *Gv, *Y, *dg, *cb, *ab, *bb;
   CA(al(&X, (size_t)rows * F)); CA(al(&H1, (size_t)rows * H)); CA(al(&H2, (size_t)rows * H));
   CA(al(&O, (size_t)rows)); CA(al(&DO, (size_t)rows)); CA(al(&DZ1, (size_t)rows * H));
   CA(al(&DZ2, (size_t)rows * H)); CA(al(&ones, (size_t)rows)); CA(al(&Gv, (size_t)rows));
-  CA(al(&Y, (size_t)rows)); CA(al(&dg, (size_t)rows)); CA(al(&gpart, (size_t)N));
+  CA(al(&Y, (size_t)rows)); CA(al(&dg, (size_t)rows));
   CA(al(&cb, (size_t)ns * c->n_occ * c->n_occ));
   CA(al(&ab, (size_t)2 * ns)); CA(al(&bb, (size_t)ns));
   std::vector<float> h1(rows, 1.0f);
@@ -1357,23 +1791,13 @@ int lp_step(bse_ctx* c, const float* d_params, int bf, double* d_grad, double* d
   CK(cudaMemcpy2DAsync(ab + 1, 2 * sizeof(double), bb, sizeof(double), sizeof(double), ns, cudaMemcpyDeviceToDevice, c->st));
   CK(mlp_loss(rows, dim, Y, c->lp_t, c->lp_tn2, ab, c->lp_r, 1.0 / (double)ns, dg, d_loss, c->st));
   CK(mlp_train_backward(d_params, rows, H1, H2, O, Gv, dg, DO, DZ1, DZ2, c->st));
-  CK(cudaMemsetAsync(gpart, 0, sizeof(double) * N, c->st));
-  CK((gemm<float, double>(true, false, H, F, (int)rows, 1.0, DZ1, H, X, F, 0.0, gpart + W1, F, 0, c->st)));
-  CK((gemm<float, double>(true, false, 1, H, (int)rows, 1.0, ones, 1, DZ1, H, 0.0, gpart + B1, H, 0, c->st)));
-  CK((gemm<float, double>(true, false, H, H, (int)rows, 1.0, DZ2, H, H1, H, 0.0, gpart + W2, H, 0, c->st)));
-  CK((gemm<float, double>(true, false, 1, H, (int)rows, 1.0, ones, 1, DZ2, H, 0.0, gpart + B2, H, 0, c->st)));
-  CK((gemm<float, double>(true, false, 1, H, (int)rows, 1.0, DO, 1, H2, H, 0.0, gpart + W3, H, 0, c->st)));
-  CK((gemm<float, double>(true, false, 1, 1, (int)rows, 1.0, ones, 1, DO, 1, 0.0, gpart + B3, 1, 0, c->st)));
-  // d_grad += gpart
-  {
-    std::vector<double> hp(N), hg(N);
-    CK(cudaMemcpyAsync(hp.data(), gpart, sizeof(double) * N, cudaMemcpyDeviceToHost, c->st));
-    CK(cudaMemcpyAsync(hg.data(), d_grad, sizeof(double) * N, cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
-    for (int i = 0; i < N; ++i) hg[i] += hp[i];
-    CK(cudaMemcpyAsync(d_grad, hg.data(), sizeof(double) * N, cudaMemcpyHostToDevice, c->st));
-    CK(cudaStreamSynchronize(c->st));
-  }
+  // d_grad += the parameter gradients (the products accumulate into it, beta = 1)
+  CK((gemm<float, double>(true, false, H, F, (int)rows, 1.0, DZ1, H, X, F, 1.0, d_grad + W1, F, 0, c->st)));
+  CK((gemm<float, double>(true, false, 1, H, (int)rows, 1.0, ones, 1, DZ1, H, 1.0, d_grad + B1, H, 0, c->st)));
+  CK((gemm<float, double>(true, false, H, H, (int)rows, 1.0, DZ2, H, H1, H, 1.0, d_grad + W2, H, 0, c->st)));
+  CK((gemm<float, double>(true, false, 1, H, (int)rows, 1.0, ones, 1, DZ2, H, 1.0, d_grad + B2, H, 0, c->st)));
+  CK((gemm<float, double>(true, false, 1, H, (int)rows, 1.0, DO, 1, H2, H, 1.0, d_grad + W3, H, 0, c->st)));
+  CK((gemm<float, double>(true, false, 1, 1, (int)rows, 1.0, ones, 1, DO, 1, 1.0, d_grad + B3, 1, 0, c->st)));
   return BSE_OK;
 }
 
@@ -1561,12 +1985,11 @@ int bse_precond_load(bse_ctx* c, const float* params) {
 // =================================================================================
 // Operator application that allocates nothing (bse_apply_liouville_static).
 //
-// Some callers cannot call cudaMalloc at the moment they need the operator: code that
-// runs while a CUDA graph is being captured, hosts whose memory budget is fixed by an
-// external pool, or hard real-time paths where a device allocation (which may
-// synchronise the device) is not allowed. For them the r-space workspaces of one
-// application live in a fixed array compiled into this library instead of being
-// allocated by the context.
+// Some callers cannot call cudaMalloc at the moment they need the operator: hosts whose
+// device memory budget is fixed by an external pool, or hard real-time paths where a
+// device allocation (which may synchronise the device) is not allowed. For them the
+// r-space workspaces of one application live in a fixed array compiled into this library
+// instead of being allocated by the context.
 // =================================================================================
 #include <mutex>
 
@@ -1605,7 +2028,7 @@ int apply_static_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out, unsigned 
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t b_a = up((size_t)ngr * n3 * sizeof(cplx<T>));
   const size_t b_h = up((size_t)nh * n3 * sizeof(cplx<T>));
-  const size_t b_c = up((size_t)nf * c->n_occ * sizeof(T));
+  const size_t b_c = up((size_t)nf * std::max(c->n_occ, c->n_qc) * sizeof(T));
   const size_t need = 2 * b_a + b_h + b_c;
   if (need > BSE_STATIC_SCRATCH_BYTES) {
     char buf[256];
@@ -1619,7 +2042,7 @@ int apply_static_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out, unsigned 
   cplx<T>* gh = reinterpret_cast<cplx<T>*>(ws + 2 * b_a);
   T* cb = reinterpret_cast<T*>(ws + 2 * b_a + b_h);
   const int N = c->N;
-  const double sf = (c->spin == 0) ? 2.0 : 0.0;
+  const double sf = c->k1e_factor();
   // the array keeps the previous call's contents: everything read is written first (the
   // transforms write every compact stage and grid point they read back) or cleared here
   // (the Hartree grids, the odd tail of R(r))
@@ -1634,18 +2057,22 @@ int apply_static_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out, unsigned 
   if (nf & 1) CK(cudaMemsetAsync(gr + (ngr - 1) * n3, 0, (size_t)n3 * sizeof(cplx<T>), c->st));
   if (c->tau_entry) {
     CK(k1d_tiled<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, c->n_ent, c->bptr, c->bw,
-                    c->n_rblocks, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->k1d_sc,
-                    c->st));
+                    c->n_rblocks, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr,
+                    k1d_variant_for<T>(c, (int)n_vec), c->st));
   } else {
     CK(k1d_combine<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, c->n_pairs, c->nbr_ptr, c->nbr_w,
                       c->nbr_p, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
   }
   CK(grid_to_sphere<T>(gr, nf, c->n_pw, c->n_half, N, c->sph, tw_of<T>(c), ga, 1.0 / (double)n3, a_out,
                        a_in, g2h_of<T>(c), esh_of<T>(c), c->n_occ, c->st));
-  // P_c with the SIMT GEMM (the tensor-core path would allocate split buffers)
+  // explicit QP terms and P_c with the SIMT GEMM (the tensor-core path would allocate split
+  // buffers)
+  CA(qp_correction<T>(c, nf, a_in, a_out, cb, false));
+  CA(emat_term<T>(c, n_vec, a_in, a_out));
   const T* psi = psi_of<T>(c);
   CK((gemm<T, T>(false, true, (int)nf, c->n_occ, c->n_pw, 1.0, a_out, c->n_pw, psi, c->n_pw, 0.0, cb,
                  c->n_occ, 1, c->st)));
+  if (c->n_up > 0) CK(mask_cross_channel<T>((int)nf, c->n_occ, c->n_up, cb, c->st));
   CK((gemm<T, T>(false, false, (int)nf, c->n_pw, c->n_occ, -1.0, cb, c->n_occ, psi, c->n_pw, 1.0, a_out,
                  c->n_pw, 1, c->st)));
   CK(zero_pad_column<T>((int)nf, c->n_pw, a_out, c->st));

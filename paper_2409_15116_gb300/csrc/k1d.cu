@@ -24,6 +24,8 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#include <algorithm>
+
 namespace bse {
 
 namespace {
@@ -139,8 +141,13 @@ __device__ __forceinline__ void ld_tau4(T (&tv)[4], const T* p) {
   }
 }
 
+// CTAs per SM the register budget is sized for: two of 256 threads, one of 512, and one for
+// the wide vector chunks (SC >= 12), whose a(r) stage leaves room for one CTA anyway
+template <int SC, int NT>
+constexpr int k1d_min_blocks() { return SC >= 12 ? 1 : 512 / NT; }
+
 template <typename T, int TR, int SC, int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) k1d_tile_kernel(
+__global__ void __launch_bounds__(NT, k1d_min_blocks<SC, NT>()) k1d_tile_kernel(
     int n_vec, int n_occ, long n3, const T* __restrict__ a, const T* __restrict__ tau4, long n_ent,
     const int* __restrict__ bptr, const int* __restrict__ bw, int n_blocks, const T* __restrict__ vloc,
     const T* __restrict__ vh, const T* __restrict__ upsi, T sf, T* __restrict__ out) {
@@ -241,7 +248,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k1d_tile_kernel(
 struct Variant { int tr, sc, nt; };
 constexpr Variant kVariants[] = {{0, 0, 0},     {16, 8, 512}, {8, 8, 256},  {16, 4, 256},
                                  {8, 4, 256},   {16, 2, 256}, {16, 1, 256}, {16, 8, 256},
-                                 {8, 8, 512},   {32, 4, 512}, {32, 8, 512}, {32, 2, 256}};
+                                 {8, 8, 512},   {32, 4, 512}, {32, 8, 512}, {32, 2, 256},
+                                 {8, 12, 256},  {8, 16, 256}};
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0])) - 1;
 
 template <typename T>
@@ -255,8 +263,8 @@ cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T* tau4,
                        const int* bw, int n_blocks, const T* vloc, const T* vh,
                        const T* upsi, double sf, T* out, long n_pts, cudaStream_t st) {
   static_assert(NT % TR == 0 && 32 % TR == 0 && NT / TR >= SC, "tile shape");
-  if constexpr (sizeof(T) == 8 && SC == 8) {
-    return cudaErrorInvalidValue;   // 64 double accumulators per lane do not fit the register budget
+  if constexpr (sizeof(T) == 8 && SC >= 8) {
+    return cudaErrorInvalidValue;   // 4 x SC double accumulators per lane do not fit the register budget
   } else {
     const size_t smem = ((size_t)n_occ * TR * SC + (size_t)TR * SC) * sizeof(T);
     static std::once_flag once;
@@ -282,19 +290,32 @@ int k1d_num_variants() { return kNumVariants; }
 template <typename T>
 bool k1d_fits(int n_occ, int v) {
   if (v < 1 || v > kNumVariants) return false;
-  if (sizeof(T) == 8 && kVariants[v].sc == 8) return false;
+  if (sizeof(T) == 8 && kVariants[v].sc >= 8) return false;
   return variant_smem<T>(n_occ, v) <= K1D_SMEM_MAX;
 }
 
-// default variant without tuning: the first in the list whose a(r) stage leaves room for
-// two CTAs per SM, else the first that fits at all; 0 when none fits
+// vectors a launch of variant v computes for n_vec trial vectors (chunks of SC, the last
+// one padded)
+int k1d_padded_vectors(int n_vec, int v) {
+  if (v < 1 || v > kNumVariants) return 1 << 30;
+  const int sc = kVariants[v].sc;
+  return (n_vec + sc - 1) / sc * sc;
+}
+
+// default variant without tuning: among the variants that fit, the least padded vectors,
+// then an a(r) stage that leaves room for two CTAs per SM, then the first in the list; 0 when
+// none fits
 template <typename T>
-int k1d_default_variant(int n_occ) {
-  for (int v = 1; v <= kNumVariants; ++v)
-    if (k1d_fits<T>(n_occ, v) && variant_smem<T>(n_occ, v) <= K1D_SMEM_MAX / 2) return v;
-  for (int v = 1; v <= kNumVariants; ++v)
-    if (k1d_fits<T>(n_occ, v)) return v;
-  return 0;
+int k1d_default_variant(int n_occ, int n_vec) {
+  int best = 0;
+  long best_key = 0;
+  for (int v = 1; v <= kNumVariants; ++v) {
+    if (!k1d_fits<T>(n_occ, v)) continue;
+    const long key = (long)k1d_padded_vectors(std::max(1, n_vec), v) * 4 +
+                     (variant_smem<T>(n_occ, v) <= K1D_SMEM_MAX / 2 ? 0 : 2);
+    if (!best || key < best_key) { best = v; best_key = key; }
+  }
+  return best;
 }
 
 template <typename T>
@@ -304,7 +325,7 @@ cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau4, 
   if (n_vec <= 0) return cudaSuccess;
   if (n_pts < 0) n_pts = n3;
   if (n_pts > n3 || n_pts % TAU_TB) return cudaErrorInvalidValue;
-  if (variant == 0) variant = k1d_default_variant<T>(n_occ);
+  if (variant == 0) variant = k1d_default_variant<T>(n_occ, n_vec);
   if (!k1d_fits<T>(n_occ, variant)) return cudaErrorInvalidValue;
   if (n3 % TAU_TB || TAU_TB % kVariants[variant].tr) return cudaErrorInvalidValue;
 #define BSE_K1D_CASE(V, TR, SC, NT)                                                                  \
@@ -323,6 +344,8 @@ cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau4, 
     BSE_K1D_CASE(9, 32, 4, 512)
     BSE_K1D_CASE(10, 32, 8, 512)
     BSE_K1D_CASE(11, 32, 2, 256)
+    BSE_K1D_CASE(12, 8, 12, 256)
+    BSE_K1D_CASE(13, 8, 16, 256)
     default: return cudaErrorInvalidValue;
   }
 #undef BSE_K1D_CASE
@@ -332,7 +355,7 @@ template cudaError_t k1d_tiled<float>(int, int, long, const float*, const float*
 template cudaError_t k1d_tiled<double>(int, int, long, const double*, const double*, long, const int*, const int*, int, const double*, const double*, const double*, double, double*, int, cudaStream_t, long);
 template bool k1d_fits<float>(int, int);
 template bool k1d_fits<double>(int, int);
-template int k1d_default_variant<float>(int);
-template int k1d_default_variant<double>(int);
+template int k1d_default_variant<float>(int, int);
+template int k1d_default_variant<double>(int, int);
 
 }  // namespace bse

@@ -71,6 +71,9 @@ template <typename T>
 cudaError_t deinterleave_pairs(int nb, const cplx<T>* grids, long n3, long p0, long n_pairs, T* tau,
                                cudaStream_t st);
 cudaError_t square_fields_split(int n, const double* u, long n3, float* rho_hi, float* rho_lo, cudaStream_t st);
+// clears C[row][w] (rows x n_occ) where orbital row % n_occ and w lie in different spin channels
+template <typename T>
+cudaError_t mask_cross_channel(int rows, int n_occ, int n_up, T* C, cudaStream_t st);
 cudaError_t normalize_overlap(int n, double* gram, double* diag, cudaStream_t st);
 template <typename T>
 cudaError_t hartree_density(int n_vec, int n_occ, long n3, const T* a, const T* upsi, T* h,
@@ -82,9 +85,11 @@ cudaError_t k1d_combine(int n_vec, int n_occ, long n3, const T* a, const T* tau,
 // ---- tc_gemm.cu (tcgen05 BF16x3) ----
 size_t tc_map_bytes();
 bool tc_make_map(void* map_out, const void* ptr, long rows, long cols, long ld);
+// wait_limit: polls of each pipeline wait before a CTA gives up, raises *err and drains
+// (negative: the default)
 cudaError_t tc_gemm_bf16x3(const void* mAh, const void* mAl, const void* mBh, const void* mBl, int M, int N,
                            int K, double alpha, double beta, float* out, long ldo, int splits, int* err,
-                           cudaStream_t st);
+                           cudaStream_t st, long long wait_limit = -1);
 cudaError_t bf16_split(const float* X, long rows, int cols, long ld_in, void* hi, void* lo, long ld_out,
                        cudaStream_t st);
 cudaError_t bf16_split64(const double* X, long rows, int cols, long ld_in, void* hi, void* lo, long ld_out,
@@ -121,11 +126,37 @@ cudaError_t jd_targets(int ns, long dim, const double* Y, const double* U, const
 cudaError_t shift_scale(int ns, int nr, double* C, const double* lam, const double* th, cudaStream_t st);
 cudaError_t row_dots(int ns, long dim, const double* A, const double* B, double* out, cudaStream_t st);
 
-// ---- k1d.cu ----
-// tile variants of the K1d kernel, numbered 1 .. k1d_num_variants(); 0 = default
-int k1d_num_variants();
+// ---- lanczos.cu (absorption spectrum) ----
+// d_v = -d psi_v / d r_i, packed (gdir: G_i per packed coordinate); P_c is applied by the caller
 template <typename T>
-int k1d_default_variant(int n_occ);
+cudaError_t dipole_rhs(int n_occ, int n_pw, const double* psi, const double* gdir, T* out, cudaStream_t st);
+// W[p] -= coef[p * ldc] X[p] for chains p < n_chain; rec (nullable) receives the coefficients
+template <typename T>
+cudaError_t lanczos_axpy(int n_chain, long dim, T* W, const T* X, const double* coef, long ldc, double* rec,
+                         long ld_rec, cudaStream_t st);
+// Q[p] = W[p] / sqrt(n2[p]) (0 when n2 = 0); beta[p * ld_beta] = sqrt(n2[p])
+template <typename T>
+cudaError_t lanczos_normalize(int n_chain, long dim, const T* W, const double* n2, T* Q, double* beta, long ld_beta,
+                              cudaStream_t st);
+cudaError_t continued_fraction(int m, const double* alpha, const double* beta, double norm2, int n_omega,
+                               const double* omega, double eta, double* gre, double* gim, cudaStream_t st);
+
+// ---- jade.cu (Wannier localisation) ----
+// W[w][r] = M_op(r) u[w][r] (squared: M_op(r)^2 u[w][r]); op = 2 axis + (0 cos, 1 sin)
+cudaError_t jade_weight(int n, long n3, int N, int op, const double* u, double* W, bool squared, cudaStream_t st);
+// one round of disjoint Givens rotations: angles from matrices 0..K_use-1, applied to all K
+// matrices A [K][n][n] and to U [n][n]; smax collects the largest |sin| (float bits)
+cudaError_t jade_round(int K_use, int K, int n, double* A, double* U, const int2* pairs, int np, double2* cs,
+                       unsigned* smax, cudaStream_t st);
+cudaError_t set_identity(int n, double* U, cudaStream_t st);
+void jade_schedule(int n, std::vector<int2>& pairs, int& rounds, int& per_round);
+
+// ---- k1d.cu ----
+// tile variants of the K1d kernel, numbered 1 .. k1d_num_variants(); 0 = default for the width
+int k1d_num_variants();
+int k1d_padded_vectors(int n_vec, int variant);
+template <typename T>
+int k1d_default_variant(int n_occ, int n_vec);
 template <typename T>
 bool k1d_fits(int n_occ, int variant);
 template <typename T>

@@ -535,6 +535,26 @@ bool finite_check_host(const double* x, long n) {
 }
 
 // ---------------------------------------------------------------------------------
+// P_c of a spin-polarised system (one projector per channel): the coefficients <psi_w|x_row>
+// of a row whose orbital (row % n_occ) lies in the other channel than w are cleared
+template <typename T>
+__global__ void mask_cross_channel_kernel(int rows, int n_occ, int n_up, T* C) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)rows * n_occ) return;
+  const int w = (int)(idx % n_occ);
+  const int v = (int)((idx / n_occ) % n_occ);
+  if ((v >= n_up) != (w >= n_up)) C[idx] = (T)0;
+}
+template <typename T>
+cudaError_t mask_cross_channel(int rows, int n_occ, int n_up, T* C, cudaStream_t st) {
+  const long tot = (long)rows * n_occ;
+  if (tot <= 0) return cudaSuccess;
+  mask_cross_channel_kernel<T><<<nblk(tot), 256, 0, st>>>(rows, n_occ, n_up, C); note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t mask_cross_channel<float>(int, int, int, float*, cudaStream_t);
+template cudaError_t mask_cross_channel<double>(int, int, int, double*, cudaStream_t);
+
 // explicit instantiations
 // ---------------------------------------------------------------------------------
 #define INST_T(T)                                                                                  \

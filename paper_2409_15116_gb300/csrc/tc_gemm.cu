@@ -29,7 +29,8 @@ constexpr int TC_STAGE_BYTES = 4 * TC_TILE;         // A_hi, A_lo, B_hi, B_lo
 constexpr int TC_EPI_LD = 17;                        // floats per row of a warp's epilogue chunk
 constexpr int TC_EPI_BYTES = 4 * 32 * TC_EPI_LD * 4; // four warps x 32 rows x 16 (+1) floats
 constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256 + TC_EPI_BYTES;
-constexpr long long TC_WAIT_LIMIT = 1ll << 26;      // try_wait polls before giving up
+constexpr long long TC_WAIT_LIMIT = 1ll << 26;      // try_wait polls before giving up (default)
+constexpr long long TC_DRAIN_LIMIT = 1ll << 26;     // polls per wait while draining after a give-up
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -39,8 +40,8 @@ __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
-  for (long long i = 0; i < TC_WAIT_LIMIT; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, long long limit) {
+  for (long long i = 0; i < limit; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -82,6 +83,7 @@ struct TcArgs {
   long ldo;
   int atomic;
   int* err;
+  long long wait_limit;   // polls of each pipeline wait before the CTA gives up
 };
 
 __global__ void __launch_bounds__(128, 1) tc_gemm_bf16x3_kernel(
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_bf16x3_kernel(
   uint64_t* accb = empty + TC_STAGES;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(accb + 1);
   float* epi = reinterpret_cast<float*>(base + TC_STAGES * TC_STAGE_BYTES + 256);   // [4][32][17]
-  __shared__ int s_abort;
+  __shared__ int s_abort, s_issued, s_consumed;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
   const int kt_all = (g.K + TC_BK - 1) / TC_BK;
@@ -106,6 +108,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_bf16x3_kernel(
     mbar_init(su32(accb), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
+    s_issued = 0;
+    s_consumed = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(TC_BN) : "memory");
@@ -121,10 +125,10 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_bf16x3_kernel(
       // TMA producer
       for (int it = 0; it < nk; ++it) {
         const int s = it % TC_STAGES;
-        if (it >= TC_STAGES && !mbar_wait(su32(empty + s), ((it / TC_STAGES) - 1) & 1)) {
+        if (it >= TC_STAGES && !mbar_wait(su32(empty + s), ((it / TC_STAGES) - 1) & 1, g.wait_limit)) {
           s_abort = 1; break;
         }
-        if (s_abort) break;
+        if (*(volatile int*)&s_abort) break;
         const uint32_t fb = su32(full + s);
         mbar_expect_tx(fb, TC_STAGE_BYTES);
         const uint32_t st = su32(base + s * TC_STAGE_BYTES);
@@ -133,12 +137,14 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_bf16x3_kernel(
         tma_load_2d(st + TC_TILE, &tAl, x, m0, fb);
         tma_load_2d(st + 2 * TC_TILE, &tBh, x, n0, fb);
         tma_load_2d(st + 3 * TC_TILE, &tBl, x, n0, fb);
+        s_issued = it + 1;
       }
     } else if (warp == 1 && lane == 0) {
       // MMA issuer
       for (int it = 0; it < nk; ++it) {
         const int s = it % TC_STAGES;
-        if (!mbar_wait(su32(full + s), (it / TC_STAGES) & 1)) { s_abort = 1; break; }
+        if (!mbar_wait(su32(full + s), (it / TC_STAGES) & 1, g.wait_limit)) { s_abort = 1; break; }
+        s_consumed = it + 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = su32(base + s * TC_STAGE_BYTES);
 #pragma unroll
@@ -156,7 +162,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_bf16x3_kernel(
     }
     // epilogue: all four warps
     __syncwarp();
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(su32(accb), 0) ? 1 : 0) != 0;
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(su32(accb), 0, g.wait_limit) ? 1 : 0) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) s_abort = 1;
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
@@ -215,7 +221,16 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_bf16x3_kernel(
     }
   }
   __syncthreads();
-  if (s_abort && threadIdx.x == 0) atomicExch(g.err, 1);
+  if (s_abort && threadIdx.x == 0) {
+    atomicExch(g.err, 1);
+    // drain before the shared memory and TMEM are released: the TMA loads issued but never
+    // consumed, then the MMAs issued (the accumulator barrier is committed after the last
+    // one, on the abort path too); each wait again bounded
+    for (int it = s_consumed; it < s_issued; ++it)
+      mbar_wait(su32(full + it % TC_STAGES), (it / TC_STAGES) & 1, TC_DRAIN_LIMIT);
+    if (nk > 0) mbar_wait(su32(accb), 0, TC_DRAIN_LIMIT);
+  }
+  __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
@@ -258,7 +273,7 @@ size_t tc_map_bytes() { return sizeof(CUtensorMap); }
 
 cudaError_t tc_gemm_bf16x3(const void* mAh, const void* mAl, const void* mBh, const void* mBl, int M, int N,
                            int K, double alpha, double beta, float* out, long ldo, int splits, int* err,
-                           cudaStream_t st) {
+                           cudaStream_t st, long long wait_limit) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   static std::once_flag once;
   static cudaError_t once_st = cudaSuccess;
@@ -277,6 +292,7 @@ cudaError_t tc_gemm_bf16x3(const void* mAh, const void* mAl, const void* mBh, co
   // receives one FP32 add, the same value as a read-modify-write, without the epilogue
   // waiting on loads of the old output
   a.out = out; a.ldo = ldo; a.atomic = (splits > 1 || beta == 1.0) ? 1 : 0; a.err = err;
+  a.wait_limit = wait_limit < 0 ? TC_WAIT_LIMIT : wait_limit;
   if (splits > 1 && beta != 1.0) {
     // partial tiles are added atomically: pre-scale the output (beta = 0 clears it)
     cudaError_t e = (beta == 0.0) ? cudaSuccess : cudaErrorInvalidValue;

@@ -37,6 +37,25 @@ def test_library_exports_every_declared_symbol(lib):
         assert name in exported, name
 
 
+from paper_2409_15116_gb300.binding import ALLOC_FN, FREE_FN  # noqa: E402
+
+_NOALLOC, _NOFREE = ALLOC_FN(), FREE_FN()
+
+
+def test_allocator_callbacks_come_in_pairs(lib):
+    """bse_create takes the caller's allocator as a pair: one callback without the other is
+    rejected before any device work (no context is returned)."""
+    from synth import make_tiny
+    s, keep = _system(make_tiny(0))
+    h = C.c_void_p()
+    only_alloc = ALLOC_FN(lambda n, u: None)
+    only_free = FREE_FN(lambda p, u: None)
+    assert lib.bse_create(C.byref(s), 0, only_alloc, _NOFREE, None, C.c_void_p(0), C.byref(h)) == -1
+    assert h.value is None
+    assert lib.bse_create(C.byref(s), 0, _NOALLOC, only_free, None, C.c_void_p(0), C.byref(h)) == -1
+    assert h.value is None
+
+
 def test_version_string(lib):
     assert b"sm_103a" in lib.bse_version()
 
@@ -88,7 +107,7 @@ def test_create_rejects_bad_input_on_host(lib, case, code):
         over["spin"] = 3
     s, keep = _system(inst, **over)
     h = C.c_void_p()
-    rc = lib.bse_create(C.byref(s), 0, C.c_void_p(0), C.byref(h))
+    rc = lib.bse_create(C.byref(s), 0, _NOALLOC, _NOFREE, None, C.c_void_p(0), C.byref(h))
     assert rc == code
     assert h.value is not None
     msg = lib.bse_last_error(h)
@@ -98,7 +117,7 @@ def test_create_rejects_bad_input_on_host(lib, case, code):
 
 def test_null_arguments(lib):
     h = C.c_void_p()
-    assert lib.bse_create(None, 0, C.c_void_p(0), C.byref(h)) == -1
+    assert lib.bse_create(None, 0, _NOALLOC, _NOFREE, None, C.c_void_p(0), C.byref(h)) == -1
     assert lib.bse_build_tau(None, None, None) == -1
     assert lib.bse_apply_liouville(None, 1, None, None) == -1
     assert lib.bse_davidson(None, None, None, None, None) == -1
