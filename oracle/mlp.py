@@ -112,3 +112,12 @@ def loss_and_grad(p, samples, project, g2p, eps, v0, shift, act_bf16=False):
     flat = np.concatenate([grads[0].ravel(), grads[1], grads[2].ravel(), grads[3], grads[4],
                            [grads[5]], np.zeros(2 * NF)])
     return L, flat
+
+
+def jd_correction(H: np.ndarray, u: np.ndarray, theta: float) -> np.ndarray:
+    """Exact Jacobi-Davidson correction of a unit Ritz vector u with Ritz value theta (the
+    training target t* of the preconditioner): t solves
+        (I - u u^T)(H - theta)(I - u u^T) t = -r,   t . u = 0,   r = (H - theta) u,
+    i.e. t = y / (u . y) - u with (H - theta) y = u (a dense solve in the e-h basis)."""
+    y = np.linalg.solve(H - theta * np.eye(H.shape[0]), u)
+    return y / (u @ y) - u

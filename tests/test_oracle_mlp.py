@@ -59,3 +59,27 @@ def test_bf16_rounding():
     vals = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -2.5, 0.0, 3.140625])
     out = mlp.bf16(vals)
     np.testing.assert_array_equal(out, [1.0, 1.0, 1.0 + 2 ** -7, -2.5, 0.0, 3.140625])
+
+
+def test_jd_correction_solves_the_correction_equation():
+    """t* = y/(u.y) - u satisfies (I - uu^T)(H - theta)(I - uu^T) t = -r and t . u = 0 for a
+    Ritz pair of the dense e-h matrix (u: a perturbed eigenvector, theta its Rayleigh
+    quotient)."""
+    from synth import make_tiny
+    from oracle import dense_eh
+    H = dense_eh.eh_hamiltonian(make_tiny(0))
+    w, X = np.linalg.eigh(H)
+    rng = np.random.default_rng(7)
+    u = X[:, 1] + 0.001 * rng.standard_normal(H.shape[0])
+    u /= np.linalg.norm(u)
+    theta = u @ H @ u
+    r = H @ u - theta * u
+    t = mlp.jd_correction(H, u, theta)
+    P = np.eye(H.shape[0]) - np.outer(u, u)
+    res = P @ ((H - theta * np.eye(H.shape[0])) @ (P @ t)) + r
+    assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(r)
+    assert abs(t @ u) <= 1e-12 * np.linalg.norm(t)
+    # the correction points the Ritz vector at the eigenvector it approximates
+    v = u + t
+    v /= np.linalg.norm(v)
+    assert 1 - abs(v @ X[:, 1]) < 1e-3 * (1 - abs(u @ X[:, 1]))
