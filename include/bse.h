@@ -259,11 +259,21 @@ int bse_solve_batch(bse_ctx* const* ctxs, int n, const bse_davidson_opts* opts, 
 /* Runs the plain solver twice on an FP64 context: once to ref_eig (<= 32) eigenpairs
  * (res_tol 1e-8), once with opts (diagonal preconditioner), capturing up to max_samples
  * (residual, Ritz value, Ritz vector) triples of the corrections it computes. Targets
- * are the exact shifted-inverse (Jacobi-Davidson) corrections t* = y/(u.y) - u with
- * y = sum_j x_j (x_j.u)/(lambda_j - theta) over the reference pairs. Replaces the
- * context's samples; *n_out (nullable) receives their number. */
+ * are the exact Jacobi-Davidson corrections t* = y/(u.y) - u, y = (L - theta)^{-1} u (the
+ * solution of (I - uu^T)(L - theta)(I - uu^T) t = -r with t.u = 0): the component of y in
+ * the span of the reference eigenvectors x_j is sum_j x_j (x_j.u)/(lambda_j - theta), the
+ * rest is solved by conjugate gradients on the complement of that span (relative residual
+ * 1e-12, where L - theta is positive definite as long as theta lies below the eigenvalues
+ * not in the reference set). Replaces the context's samples; *n_out (nullable) receives
+ * their number. */
 int bse_precond_collect(bse_ctx* ctx, const bse_davidson_opts* opts, int ref_eig, int max_samples,
                         int* n_out);
+
+/* Copies up to n of the context's samples to host arrays (each nullable): u_out, r_out,
+ * t_out [n][n_occ][n_pw] (Ritz vectors -- only for samples from bse_precond_collect --,
+ * residuals, targets), theta_out [n]; *n_out (nullable) = samples held. */
+int bse_precond_get_samples(bse_ctx* ctx, int n, double* u_out, double* r_out, double* t_out, double* theta_out,
+                            int* n_out);
 
 /* Replaces the context's samples with caller data: host [n][n_occ][n_pw] residuals r and
  * targets t, host [n] Ritz values theta (FP64). */

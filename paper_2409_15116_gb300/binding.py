@@ -28,7 +28,7 @@ EXPORTS = ["bse_create", "bse_build_tau", "bse_get_pairs", "bse_get_overlaps",
            "bse_destroy", "bse_profile", "bse_profile_read", "bse_apply_liouville_static",
            "bse_precond_collect", "bse_precond_set_samples", "bse_precond_grad",
            "bse_precond_train", "bse_precond_load", "bse_solve_batch", "bse_lanczos",
-           "bse_lanczos_spectrum", "bse_localize"]
+           "bse_lanczos_spectrum", "bse_localize", "bse_precond_get_samples"]
 NPARAM = 4619
 
 
@@ -133,6 +133,7 @@ def load(path: str = LIB_PATH):
     F = C.POINTER(C.c_float)
     lib.bse_precond_collect.argtypes = [P, C.POINTER(DavidsonOpts), C.c_int, C.c_int, C.POINTER(C.c_int)]
     lib.bse_precond_set_samples.argtypes = [P, C.c_int, D, D, D]
+    lib.bse_precond_get_samples.argtypes = [P, C.c_int, D, D, D, D, C.POINTER(C.c_int)]
     lib.bse_precond_grad.argtypes = [P, F, C.c_int, D, D]
     lib.bse_precond_train.argtypes = [C.POINTER(P), C.c_int, F, C.c_int, C.c_double, C.c_int, F, D]
     lib.bse_precond_load.argtypes = [P, F]
@@ -323,6 +324,18 @@ class Context:
         n = C.c_int()
         self._check(self.lib.bse_precond_collect(self.h, C.byref(opts), ref_eig, max_samples, C.byref(n)))
         return int(n.value)
+
+    def precond_get_samples(self, with_u=True):
+        """(u, r, t, theta) of the context's samples (u is None for caller samples)."""
+        n = C.c_int()
+        self._check(self.lib.bse_precond_get_samples(self.h, 0, None, None, None, None, C.byref(n)))
+        ns = n.value
+        shape = (ns, self.n_occ, self.n_pw)
+        u = np.zeros(shape) if with_u else None
+        r, t, th = np.zeros(shape), np.zeros(shape), np.zeros(ns)
+        self._check(self.lib.bse_precond_get_samples(self.h, ns, _dptr(u) if with_u else None, _dptr(r), _dptr(t),
+                                                     _dptr(th), C.byref(n)))
+        return u, r, t, th
 
     def precond_set_samples(self, r, t, theta):
         r = np.ascontiguousarray(r, dtype=np.float64)

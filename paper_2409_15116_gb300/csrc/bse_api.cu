@@ -99,7 +99,9 @@ struct bse_ctx {
   float* lp_params = nullptr;
   int* d_bad = nullptr;
   long lp_ns = 0;                      // samples held
+  int lp_cg_iters = 0;                 // CG iterations of the last exact-target solve
   double *lp_r = nullptr, *lp_t = nullptr, *lp_theta = nullptr, *lp_rn2 = nullptr, *lp_tn2 = nullptr;
+  double* lp_u = nullptr;              // Ritz vectors of the collected samples (null for caller samples)
   // problem
   int N = 0;
   long n3 = 0;
@@ -604,8 +606,8 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
 // ---------------------------------------------------------------------------------
 // overlaps, pair rule and screened integrals (Eqs. overlap, tau, tau_from_tau_u, pdep)
 // ---------------------------------------------------------------------------------
-// contexts inside build_tau at this moment (process-wide)
-std::atomic<int> g_tau_builders{0};
+// serialises the tau layout decision and allocation of contexts building at the same time
+std::mutex g_tau_layout_mu;
 
 template <typename T>
 int build_tau_impl(bse_ctx* c) {
@@ -713,25 +715,26 @@ int build_tau_impl(bse_ctx* c) {
   // about 2.8 times the per-pair values, so it is used only while it takes at most half of
   // the free device memory (large FP64 systems keep the per-pair layout);
   // BSE_TAU_LAYOUT=pair forces the per-pair layout and the untiled kernel.
-  // Contexts that build tau at the same time (bse_solve_batch) share the free memory: each
-  // takes at most its share of the half.
+  // Contexts that build tau at the same time (bse_solve_batch) take the layout decision and
+  // the allocation one after another, so each sees the memory the earlier ones took.
   T* tau;
   {
+    std::lock_guard<std::mutex> lk(g_tau_layout_mu);
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
     const double t4 = (double)c->n_ent * 4.0 * (double)n3 * sizeof(T);
     const char* lay = getenv("BSE_TAU_LAYOUT");
     const bool force_pair = lay && std::strcmp(lay, "pair") == 0;
-    const int builders = std::max(1, g_tau_builders.load());
     c->tau_entry = !force_pair && k1d_default_variant<T>(c->n_occ, 1) > 0 && n3 % TAU_TB == 0 &&
-                   t4 <= 0.5 * (double)fr / builders;
+                   t4 <= 0.5 * (double)fr;
+    if (c->tau_entry) {
+      CA(dalloc(c, &tau, (size_t)c->n_ent * 4 * n3));
+    } else {
+      CA(dalloc(c, &tau, (size_t)c->n_pairs * n3));
+    }
+    CK(cudaStreamSynchronize(c->st));   // the allocation is visible in the next context's free memory
   }
-  if (c->tau_entry) {
-    CA(dalloc(c, &tau, (size_t)c->n_ent * 4 * n3));
-    CK(cudaMemsetAsync(tau, 0, sizeof(T) * (size_t)c->n_ent * 4 * n3, c->st));
-  } else {
-    CA(dalloc(c, &tau, (size_t)c->n_pairs * n3));
-  }
+  if (c->tau_entry) CK(cudaMemsetAsync(tau, 0, sizeof(T) * (size_t)c->n_ent * 4 * n3, c->st));
   c->tau = tau;
   const size_t budget = (size_t)2 << 30;
   long nb = (long)(budget / (n3 * sizeof(cplx<T>))) * 2;
@@ -1579,9 +1582,7 @@ static int check_device_flag(bse_ctx* c) {
 
 int bse_build_tau(bse_ctx* c, int64_t* n_pairs_out, double* thr_out) {
   if (!c) return BSE_ERR_INVALID_ARG;
-  ++g_tau_builders;
   int r = (c->prec == BSE_PREC_FP64) ? build_tau_impl<double>(c) : build_tau_impl<float>(c);
-  --g_tau_builders;
   cudaStreamSynchronize(c->st);
   c->prof.resolve();
   if (r != BSE_OK) return r;
@@ -1740,7 +1741,8 @@ namespace {
 
 void lp_free_samples(bse_ctx* c) {
   dfree(c, c->lp_r); dfree(c, c->lp_t); dfree(c, c->lp_theta); dfree(c, c->lp_rn2); dfree(c, c->lp_tn2);
-  c->lp_r = c->lp_t = c->lp_theta = c->lp_rn2 = c->lp_tn2 = nullptr;
+  dfree(c, c->lp_u);
+  c->lp_r = c->lp_t = c->lp_theta = c->lp_rn2 = c->lp_tn2 = c->lp_u = nullptr;
   c->lp_ns = 0;
 }
 
@@ -1861,17 +1863,80 @@ int bse_precond_collect(bse_ctx* c, const bse_davidson_opts* o, int ref_eig, int
   if (r != BSE_OK && r != BSE_ERR_NOT_CONVERGED) return r;
   const int ns = (int)thetas.size();
   if (ns == 0) return fail(c, BSE_ERR_STATE, "no samples: the solver converged before any correction");
-  // targets t* = y/(u.y) - u with y = sum_j x_j (x_j . u)/(lambda_j - theta)
+  // Exact Jacobi-Davidson targets t* = y/(u.y) - u with y = (L - theta)^{-1} u. The part of
+  // y in the span of the reference eigenvectors is the exact sum
+  // sum_j x_j (x_j.u)/(lambda_j - theta); the rest z solves (L - theta) z = u - X X^T u on
+  // the complement of that span, where L - theta is positive definite (theta lies below the
+  // eigenvalues not in the reference set), by conjugate gradients with deflation, every
+  // sample a column of one block (one operator application per CG iteration).
   CA(lp_alloc_samples(c, ns));
-  double *Cm, *uy, *th_d;
+  double *Cm, *uy, *th_d, *Z, *Rc, *Pc, *Qc, *coef, *dots;
   CA(dalloc(c, &Cm, (size_t)ns * ref_eig));
   CA(dalloc(c, &uy, (size_t)ns));
   CA(dalloc(c, &th_d, (size_t)ns));
-  struct G5 { bse_ctx* c; void* a; void* b; void* d; ~G5() { dfree(c, a); dfree(c, b); dfree(c, d); } } g5{c, Cm, uy, th_d};
+  CA(dalloc(c, &Z, (size_t)ns * dim)); CA(dalloc(c, &Rc, (size_t)ns * dim));
+  CA(dalloc(c, &Pc, (size_t)ns * dim)); CA(dalloc(c, &Qc, (size_t)ns * dim));
+  CA(dalloc(c, &coef, (size_t)ns)); CA(dalloc(c, &dots, (size_t)ns));
+  struct G5 { bse_ctx* c; std::vector<void*> v; ~G5() { for (void* x : v) dfree(c, x); } } g5{c, {Cm, uy, th_d, Z, Rc, Pc, Qc, coef, dots}};
   CK(cudaMemcpyAsync(th_d, thetas.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, c->st));
+  // low part: y_low = X diag(1/(lambda - theta)) X^T u (into lp_t)
   CK((gemm<double, double>(false, true, ns, ref_eig, (int)dim, 1.0, U, dim, Xr, dim, 0.0, Cm, ref_eig, 0, c->st)));
+  // rhs of the complement: b = u - X (X^T u) (into Rc), before Cm is scaled
+  CK(cudaMemcpyAsync(Rc, U, sizeof(double) * ns * dim, cudaMemcpyDeviceToDevice, c->st));
+  CK((gemm<double, double>(false, false, ns, (int)dim, ref_eig, -1.0, Cm, ref_eig, Xr, dim, 1.0, Rc, dim, 1, c->st)));
   CK(shift_scale(ns, ref_eig, Cm, lam, th_d, c->st));
   CK((gemm<double, double>(false, false, ns, (int)dim, ref_eig, 1.0, Cm, ref_eig, Xr, dim, 0.0, c->lp_t, dim, 1, c->st)));
+  // CG: z = 0, r = b, p = r
+  CK(cudaMemsetAsync(Z, 0, sizeof(double) * ns * dim, c->st));
+  CK(cudaMemcpyAsync(Pc, Rc, sizeof(double) * ns * dim, cudaMemcpyDeviceToDevice, c->st));
+  std::vector<double> rr(ns), rr0(ns), pq(ns), hc(ns);
+  CK(row_norms2<double>(ns, dim, Rc, dots, c->st));
+  CK(cudaMemcpyAsync(rr.data(), dots, sizeof(double) * ns, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  rr0 = rr;
+  std::vector<char> done(ns, 0);
+  const double cg_tol = 1e-12;
+  int cg_it = 0;
+  for (; cg_it < 2000; ++cg_it) {
+    bool all = true;
+    for (int i = 0; i < ns; ++i) {
+      if (!done[i] && rr[i] <= cg_tol * cg_tol * rr0[i]) done[i] = 1;
+      all = all && done[i];
+    }
+    if (all) break;
+    // q = (L - theta) p, deflated
+    CA(apply_impl<double>(c, ns, Pc, Qc));
+    CK(lanczos_axpy<double>(ns, dim, Qc, Pc, th_d, 1, nullptr, 0, c->st));
+    CK((gemm<double, double>(false, true, ns, ref_eig, (int)dim, 1.0, Qc, dim, Xr, dim, 0.0, Cm, ref_eig, 0, c->st)));
+    CK((gemm<double, double>(false, false, ns, (int)dim, ref_eig, -1.0, Cm, ref_eig, Xr, dim, 1.0, Qc, dim, 1, c->st)));
+    CK(row_dots(ns, dim, Pc, Qc, dots, c->st));
+    CK(cudaMemcpyAsync(pq.data(), dots, sizeof(double) * ns, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    // z += alpha p, r -= alpha q (alpha = 0 for converged columns)
+    for (int i = 0; i < ns; ++i) hc[i] = (done[i] || !(pq[i] > 0)) ? 0.0 : -rr[i] / pq[i];
+    CK(cudaMemcpyAsync(coef, hc.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, c->st));
+    CK(lanczos_axpy<double>(ns, dim, Z, Pc, coef, 1, nullptr, 0, c->st));
+    for (int i = 0; i < ns; ++i) hc[i] = -hc[i];
+    CK(cudaMemcpyAsync(coef, hc.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, c->st));
+    CK(lanczos_axpy<double>(ns, dim, Rc, Qc, coef, 1, nullptr, 0, c->st));
+    CK(row_norms2<double>(ns, dim, Rc, dots, c->st));
+    std::vector<double> rn(ns);
+    CK(cudaMemcpyAsync(rn.data(), dots, sizeof(double) * ns, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    // p = r + beta p
+    for (int i = 0; i < ns; ++i) hc[i] = (done[i] || !(rr[i] > 0)) ? 1.0 : rn[i] / rr[i];
+    CK(cudaMemcpyAsync(coef, hc.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, c->st));
+    CK(scale_rows<double>(ns, dim, Pc, coef, c->st));
+    for (int i = 0; i < ns; ++i) hc[i] = done[i] ? 0.0 : -1.0;
+    CK(cudaMemcpyAsync(coef, hc.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, c->st));
+    CK(lanczos_axpy<double>(ns, dim, Pc, Rc, coef, 1, nullptr, 0, c->st));
+    for (int i = 0; i < ns; ++i) if (!done[i]) rr[i] = rn[i];
+  }
+  c->lp_cg_iters = cg_it;
+  // y = y_low + z; t* = y/(u.y) - u
+  std::vector<double> ones(ns, -1.0);
+  CK(cudaMemcpyAsync(coef, ones.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, c->st));
+  CK(lanczos_axpy<double>(ns, dim, c->lp_t, Z, coef, 1, nullptr, 0, c->st));
   CK(row_dots(ns, dim, U, c->lp_t, uy, c->st));
   CK(jd_targets(ns, dim, c->lp_t, U, uy, c->lp_t, c->st));
   {
@@ -1881,11 +1946,32 @@ int bse_precond_collect(bse_ctx* c, const bse_davidson_opts* o, int ref_eig, int
     dfree(c, cb);
     if (rp != BSE_OK) return rp;
   }
+  CA(dalloc(c, &c->lp_u, (size_t)ns * dim));
+  CK(cudaMemcpyAsync(c->lp_u, U, sizeof(double) * ns * dim, cudaMemcpyDeviceToDevice, c->st));
   CK(cudaMemcpyAsync(c->lp_r, R, sizeof(double) * ns * dim, cudaMemcpyDeviceToDevice, c->st));
   CK(cudaMemcpyAsync(c->lp_theta, th_d, sizeof(double) * ns, cudaMemcpyDeviceToDevice, c->st));
   CA(lp_finish_samples(c));
   CK(cudaStreamSynchronize(c->st));
   if (n_out) *n_out = ns;
+  return BSE_OK;
+}
+
+int bse_precond_get_samples(bse_ctx* c, int n, double* u_out, double* r_out, double* t_out, double* theta_out,
+                            int* n_out) {
+  if (!c) return BSE_ERR_INVALID_ARG;
+  if (n < 0) return fail(c, BSE_ERR_INVALID_ARG, "bse_precond_get_samples: n < 0");
+  const long dim = (long)c->n_occ * c->n_pw;
+  const long k = std::min<long>(n, c->lp_ns);
+  if (n_out) *n_out = (int)c->lp_ns;
+  if (k == 0) return BSE_OK;
+  if (u_out) {
+    if (!c->lp_u) return fail(c, BSE_ERR_STATE, "the samples were set by the caller: no Ritz vectors held");
+    CK(cudaMemcpyAsync(u_out, c->lp_u, sizeof(double) * k * dim, cudaMemcpyDeviceToHost, c->st));
+  }
+  if (r_out) CK(cudaMemcpyAsync(r_out, c->lp_r, sizeof(double) * k * dim, cudaMemcpyDeviceToHost, c->st));
+  if (t_out) CK(cudaMemcpyAsync(t_out, c->lp_t, sizeof(double) * k * dim, cudaMemcpyDeviceToHost, c->st));
+  if (theta_out) CK(cudaMemcpyAsync(theta_out, c->lp_theta, sizeof(double) * k, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
   return BSE_OK;
 }
 

@@ -41,3 +41,22 @@ def test_batch_matches_individual_solves_and_oracle():
     Lop = liouville.Liouville(inst)
     want, _, info = davidson.davidson(Lop.apply, Lop.diagonal(), Lop.project, 4, 8, 32, 1e-7)
     assert np.abs(om[0] - want).max() <= 1e-7
+
+
+def test_mixed_batch_against_the_oracle_davidson():
+    """The mixed-precision batch (FP32 operator, BF16x3 projections): every system's lowest
+    excitations within 1 meV of the oracle's FP64 Davidson on the matrix-free operator."""
+    from paper_2409_15116_gb300 import Context, binding
+    MEV = 3.6749322e-5
+    systems = _systems()[:4]
+    streams = [torch.cuda.Stream() for _ in systems]
+    ctxs = [Context(inst, 1, stream=st.cuda_stream) for inst, st in zip(systems, streams)]
+    om, stats, rc = binding.solve_batch(ctxs, 4, 8, 32, res_tol=1e-4)
+    assert all(r == 0 for r in rc), rc
+    for c in ctxs:
+        c.close()
+    for i, inst in enumerate(systems):
+        Lop = liouville.Liouville(inst)
+        want, _, info = davidson.davidson(Lop.apply, Lop.diagonal(), Lop.project, 4, 8, 32, 1e-7)
+        assert info["converged"]
+        assert np.abs(om[i] - want).max() <= MEV, (i, om[i] - want)
