@@ -302,12 +302,23 @@ def main():
     metric = "time_to_16_lowest_VEEs_1meV_vs_fp64_plain"
     probe = CONFIGS[args.config if not args.batch else "tiny"]()
     n_g = 2 * probe.n_half - 1
+    # solver shape: the medium workload's block of 32 (subspace 128); the large one (96^3,
+    # 1,024 orbitals, ~20k pairs) uses its block of 64 with a subspace of 96 to leave room
+    # for its 71 GB of tau
+    global BLOCK, MAX_SUB
+    if args.config == "large":
+        BLOCK, MAX_SUB = 64, 96
+    pairs_desc = "~20k pairs" if args.config == "large" else "15% of pairs"
     cfg_desc = {"workload": f"{args.config}: L={probe.L:g} bohr, {probe.n_grid}^3 grid, N_G={n_g}, "
-                            f"N_occ={probe.n_occ}, N_pdep={probe.n_pdep}, 15% of pairs, {N_EIG} VEEs, "
+                            f"N_occ={probe.n_occ}, N_pdep={probe.n_pdep}, {pairs_desc}, {N_EIG} VEEs, "
                             f"Davidson block {BLOCK}, mixed FP32/FP64",
                 "grid": probe.n_grid, "n_occ": probe.n_occ, "n_pdep": probe.n_pdep, "n_eig": N_EIG,
                 "block": BLOCK,
                 "l2": "inputs larger than L2 (tau and r-space workspaces exceed 129 MB)"}
+    if args.config == "large":
+        # one GPU cannot hold a second large context (e2e), the FP64 plain solve (142 GB of tau
+        # plus an FP64 subspace) or, on the host, the FP64 oracle's tau (142 GB)
+        args.no_e2e = args.no_fp64 = args.no_cpu = args.no_batch_line = True
 
     if args.impl == "reference":
         if rank != 0:

@@ -236,9 +236,10 @@ int bse_lanczos_spectrum(bse_ctx* ctx, int n_steps, const double* alpha, const d
 /* Batched solves (library addition; the paper distributes one system over many GPUs,
  * Section 3): for each of n independent contexts -- typically many small systems of
  * uneven grid and orbital counts -- builds tau if needed and runs bse_davidson with the
- * same options, all concurrently, one host thread per context. Contexts created on
- * distinct CUDA streams run their kernels concurrently on the device; contexts sharing a
- * stream serialise. omega_out: host [n][opts->n_eig]; stats (nullable): host [n];
+ * same options. A pool of host threads (BSE_BATCH_WORKERS, default 16) takes the systems in
+ * order, one thread per system at a time; a system that runs out of device memory is solved
+ * again, alone, after the others. Contexts created on distinct CUDA streams run their
+ * kernels concurrently on the device; contexts sharing a stream serialise. omega_out: host [n][opts->n_eig]; stats (nullable): host [n];
  * status_out (nullable): host [n] per-system status. Returns BSE_OK or the first
  * failing status. */
 int bse_solve_batch(bse_ctx* const* ctxs, int n, const bse_davidson_opts* opts, double* omega_out,

@@ -1685,19 +1685,32 @@ int bse_solve_batch(bse_ctx* const* ctxs, int n, const bse_davidson_opts* o, dou
   int dev = 0;
   cudaGetDevice(&dev);
   std::vector<int> rc(n, BSE_OK);
+  // A pool of worker threads takes the systems in order from a shared counter (at most
+  // BSE_BATCH_WORKERS at a time, default 16), each driving its context's stream, so the
+  // number of systems holding workspaces at once stays bounded. A system whose solve ran out
+  // of device memory is solved again after the pool has finished, alone.
+  int workers = 16;
+  if (const char* e = getenv("BSE_BATCH_WORKERS")) workers = std::max(1, atoi(e));
+  workers = std::min(workers, n);
+  std::atomic<int> next{0};
+  auto solve_one = [&](int i) {
+    bse_ctx* c = ctxs[i];
+    int r = BSE_OK;
+    if (!c->tau_ready) r = bse_build_tau(c, nullptr, nullptr);
+    if (r == BSE_OK) r = bse_davidson(c, o, omega_out + (size_t)i * o->n_eig, nullptr, stats ? stats + i : nullptr);
+    rc[i] = r;
+  };
   std::vector<std::thread> th;
-  th.reserve(n);
-  for (int i = 0; i < n; ++i) {
-    th.emplace_back([&, i] {
+  th.reserve(workers);
+  for (int k = 0; k < workers; ++k) {
+    th.emplace_back([&] {
       cudaSetDevice(dev);
-      bse_ctx* c = ctxs[i];
-      int r = BSE_OK;
-      if (!c->tau_ready) r = bse_build_tau(c, nullptr, nullptr);
-      if (r == BSE_OK) r = bse_davidson(c, o, omega_out + (size_t)i * o->n_eig, nullptr, stats ? stats + i : nullptr);
-      rc[i] = r;
+      for (int i = next++; i < n; i = next++) solve_one(i);
     });
   }
   for (auto& t : th) t.join();
+  for (int i = 0; i < n; ++i)
+    if (rc[i] == BSE_ERR_OOM) solve_one(i);
   int first = BSE_OK;
   for (int i = 0; i < n; ++i) {
     if (status_out) status_out[i] = rc[i];
