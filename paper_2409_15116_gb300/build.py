@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libbse.so")
-SOURCES = ["fft.cu", "gemm.cu", "ops.cu", "k1d.cu", "eigh.cu", "tc_gemm.cu", "precond.cu", "lanczos.cu",
+SOURCES = ["fft.cu", "gemm.cu", "ops.cu", "k1d.cu", "k1d_sym.cu", "eigh.cu", "tc_gemm.cu", "precond.cu", "lanczos.cu",
            "jade.cu", "bse_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

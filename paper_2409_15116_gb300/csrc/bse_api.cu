@@ -145,6 +145,14 @@ struct bse_ctx {
   int n_rblocks = 0;
   int64_t n_ent = 0;
   bool tau_entry = false;    // tau stored entry-major for the tiled K1d kernel
+  // tau stored once per pair for the symmetric-layout tiled kernel (when the entry-major one
+  // would not fit): upper entries and transposed tiles of every row block
+  bool tau_sym = false;
+  int *ubptr = nullptr, *ubw = nullptr, *utptr = nullptr, *utinfo = nullptr;
+  int4* utent = nullptr;
+  int2* uslot = nullptr;
+  int64_t n_ent_u = 0;
+  std::map<int, int> k1d_var_sym;
   // K1d tile variant per block width n_vec, chosen by the autotuner (absent: not tuned yet)
   std::map<int, int> k1d_var;
   int k1d_force = 0;         // BSE_K1D_VARIANT: one variant for every width, no tuning
@@ -516,6 +524,56 @@ int autotune_k1d(bse_ctx* c, int nv, long n3, const T* ga, const T* gh, T* gr, d
   return BSE_OK;
 }
 
+// the same tuning for the symmetric-layout kernel (its own variant list)
+std::map<std::tuple<int, long, int, long, int>, int> g_k1d_sym_tuned;
+K1dLists k1d_sym_lists(const bse_ctx* c);
+
+template <typename T>
+int k1d_sym_variant_for(const bse_ctx* c, int nv) {
+  auto it = c->k1d_var_sym.find(nv);
+  return it != c->k1d_var_sym.end() ? it->second : k1d_sym_default_variant<T>(c->n_occ, nv);
+}
+
+template <typename T>
+int autotune_k1d_sym(bse_ctx* c, int nv, long n3, const T* ga, const T* gh, T* gr, double sf) {
+  if (!c->autotune) { c->k1d_var_sym[nv] = k1d_sym_default_variant<T>(c->n_occ, nv); return BSE_OK; }
+  const auto key = std::make_tuple((int)sizeof(T), n3, c->n_occ, (long)c->n_ent_u, nv);
+  {
+    std::lock_guard<std::mutex> lk(g_k1d_tune_mu);
+    auto it = g_k1d_sym_tuned.find(key);
+    if (it != g_k1d_sym_tuned.end()) { c->k1d_var_sym[nv] = it->second; return BSE_OK; }
+  }
+  const long n_pts = std::max<long>(TAU_TB, (n3 / 8) / TAU_TB * TAU_TB);
+  int least = 1 << 30;
+  for (int v = 1; v <= k1d_sym_num_variants(); ++v)
+    if (k1d_sym_fits<T>(c->n_occ, v)) least = std::min(least, k1d_sym_padded_vectors(nv, v));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_v = 0;
+  const K1dLists L = k1d_sym_lists(c);
+  for (int v = 1; v <= k1d_sym_num_variants(); ++v) {
+    if (!k1d_sym_fits<T>(c->n_occ, v) || k1d_sym_padded_vectors(nv, v) > least + 3) continue;
+    float t = 0;
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(cudaEventRecord(e0, c->st));
+      CK(k1d_sym_tiled<T>(nv, c->n_occ, n3, ga, (const T*)c->tau, L, vloc_of<T>(c), gh, upsi_of<T>(c), sf, gr, v,
+                          c->st, n_pts));
+      CK(cudaEventRecord(e1, c->st));
+      CK(cudaEventSynchronize(e1));
+      CK(cudaEventElapsedTime(&t, e0, e1));
+    }
+    if (t < best) { best = t; best_v = v; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->k1d_var_sym[nv] = best_v ? best_v : k1d_sym_default_variant<T>(c->n_occ, nv);
+  std::lock_guard<std::mutex> lk(g_k1d_tune_mu);
+  g_k1d_sym_tuned[key] = c->k1d_var_sym[nv];
+  return BSE_OK;
+}
+
 // ---------------------------------------------------------------------------------
 // R = P_c (D + K1e - K1d) A   (Eqs. evp, d, k1e, k1d)
 // ---------------------------------------------------------------------------------
@@ -571,6 +629,11 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
         CK(k1d_tiled<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->n_ent, c->bptr, c->bw, c->n_rblocks,
                         vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, k1d_variant_for<T>(c, (int)nv),
                         c->st));
+      } else if (c->tau_sym) {
+        if (!c->k1d_var_sym.count((int)nv))
+          CA(autotune_k1d_sym<T>(c, (int)nv, n3, (const T*)ga, (const T*)gh, (T*)gr, sf));
+        CK(k1d_sym_tiled<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, k1d_sym_lists(c), vloc_of<T>(c),
+                            (const T*)gh, upsi_of<T>(c), sf, (T*)gr, k1d_sym_variant_for<T>(c, (int)nv), c->st));
       } else {
         CK(k1d_combine<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, c->n_pairs, c->nbr_ptr, c->nbr_w, c->nbr_p,
                           vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));
@@ -608,6 +671,86 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
 // ---------------------------------------------------------------------------------
 // serialises the tau layout decision and allocation of contexts building at the same time
 std::mutex g_tau_layout_mu;
+
+// lists of the symmetric (once per pair) tau layout; pid[v][w] = pair index or -1
+int build_sym_lists(bse_ctx* c, const std::vector<std::vector<int>>& pid) {
+  const int n = c->n_occ;
+  const int nrb = (n + 3) / 4;
+  int64_t n_ent_u = 0;
+  std::vector<int2> hslot_u;
+  // Row blocks of 4 consecutive orbitals. Upper entries of block b: every w >= 4b that pairs
+  // with a row of b (Eq. overlap); tau_vw = tau_wv (Eq. tau), so the rows' neighbours in
+  // earlier blocks are read from those blocks' entries as transposed tiles.
+    std::vector<int> ubptr_h(1, 0), ubw_h;
+  std::vector<int> ent_of((size_t)nrb * n, -1);   // entry index of (block, w), -1 if none
+  for (int b = 0; b < nrb; ++b) {
+    for (int w = 4 * b; w < n; ++w) {
+      bool any = false;
+      for (int i = 0; i < 4; ++i) {
+        const int v = 4 * b + i;
+        if (v < n && pid[v][w] >= 0) any = true;
+      }
+      if (any) { ent_of[(size_t)b * n + w] = (int)ubw_h.size(); ubw_h.push_back(w); }
+    }
+    ubptr_h.push_back((int)ubw_h.size());
+  }
+  std::vector<int> utptr_h(1, 0), utinfo_h;
+  std::vector<int4> utent_h;
+  for (int b = 0; b < nrb; ++b) {
+    for (int J = 0; J < b; ++J) {
+      int4 q = make_int4(-1, -1, -1, -1);
+      int* qq = &q.x;
+      int jm = 0;
+      for (int i = 0; i < 4; ++i) {
+        const int v = 4 * b + i;
+        if (v >= n) continue;
+        qq[i] = ent_of[(size_t)J * n + v];
+        for (int j = 0; j < 4; ++j)
+          if (4 * J + j < n && pid[4 * J + j][v] >= 0) jm |= 1 << j;
+      }
+      if (jm) { utinfo_h.push_back((J << 4) | jm); utent_h.push_back(q); }
+    }
+    utptr_h.push_back((int)utinfo_h.size());
+  }
+  n_ent_u = (int64_t)ubw_h.size();
+  // entry slots of every pair v <= w: row v % 4 of entry (block of v, w); inside one block
+  // also row w % 4 of entry (block, v), since that block's rows read both from their own
+  // entries
+  hslot_u.assign(c->n_pairs, make_int2(-1, -1));
+  for (int64_t p = 0; p < c->n_pairs; ++p) {
+    const int v = c->pv_h[p], w = c->pw_h[p];
+    const int bv = v / 4, bw_ = w / 4;
+    hslot_u[p].x = 4 * ent_of[(size_t)bv * n + w] + v % 4;
+    if (bv == bw_ && v != w) hslot_u[p].y = 4 * ent_of[(size_t)bv * n + v] + w % 4;
+  }
+  c->n_ent_u = n_ent_u;
+  dfree(c, c->ubptr); dfree(c, c->ubw); dfree(c, c->utptr); dfree(c, c->utinfo); dfree(c, c->utent); dfree(c, c->uslot);
+  c->ubptr = c->ubw = c->utptr = c->utinfo = nullptr; c->utent = nullptr; c->uslot = nullptr;
+  CA(dalloc(c, &c->ubptr, ubptr_h.size()));
+  CA(dalloc(c, &c->ubw, std::max<size_t>(1, ubw_h.size())));
+  CA(dalloc(c, &c->utptr, utptr_h.size()));
+  CA(dalloc(c, &c->utinfo, std::max<size_t>(1, utinfo_h.size())));
+  CA(dalloc(c, &c->utent, std::max<size_t>(1, utent_h.size())));
+  CA(dalloc(c, &c->uslot, hslot_u.size()));
+  CK(cudaMemcpyAsync(c->ubptr, ubptr_h.data(), sizeof(int) * ubptr_h.size(), cudaMemcpyHostToDevice, c->st));
+  if (!ubw_h.empty()) CK(cudaMemcpyAsync(c->ubw, ubw_h.data(), sizeof(int) * ubw_h.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->utptr, utptr_h.data(), sizeof(int) * utptr_h.size(), cudaMemcpyHostToDevice, c->st));
+  if (!utinfo_h.empty()) {
+    CK(cudaMemcpyAsync(c->utinfo, utinfo_h.data(), sizeof(int) * utinfo_h.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->utent, utent_h.data(), sizeof(int4) * utent_h.size(), cudaMemcpyHostToDevice, c->st));
+  }
+  CK(cudaMemcpyAsync(c->uslot, hslot_u.data(), sizeof(int2) * hslot_u.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return BSE_OK;
+}
+
+K1dLists k1d_sym_lists(const bse_ctx* c) {
+  K1dLists L;
+  L.n_ent = (long)c->n_ent_u;
+  L.n_blocks = c->n_rblocks;
+  L.bptr = c->ubptr; L.bw = c->ubw; L.tptr = c->utptr; L.tinfo = c->utinfo; L.tent = c->utent;
+  return L;
+}
 
 template <typename T>
 int build_tau_impl(bse_ctx* c) {
@@ -715,26 +858,40 @@ int build_tau_impl(bse_ctx* c) {
   // about 2.8 times the per-pair values, so it is used only while it takes at most half of
   // the free device memory (large FP64 systems keep the per-pair layout);
   // BSE_TAU_LAYOUT=pair forces the per-pair layout and the untiled kernel.
-  // Contexts that build tau at the same time (bse_solve_batch) take the layout decision and
-  // the allocation one after another, so each sees the memory the earlier ones took.
+  // Layout: the ordered entry-major tau where it takes at most half of the free memory, else
+  // the symmetric one (each pair once) where that fits, else the per-pair layout with the
+  // untiled kernel; BSE_TAU_LAYOUT=upper or pair skips the earlier choices. Contexts that
+  // build tau at the same time (bse_solve_batch) take the decision and the allocation one
+  // after another, so each sees the memory the earlier ones took.
   T* tau;
   {
     std::lock_guard<std::mutex> lk(g_tau_layout_mu);
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
-    const double t4 = (double)c->n_ent * 4.0 * (double)n3 * sizeof(T);
+    const double half = 0.5 * (double)fr;
     const char* lay = getenv("BSE_TAU_LAYOUT");
     const bool force_pair = lay && std::strcmp(lay, "pair") == 0;
-    c->tau_entry = !force_pair && k1d_default_variant<T>(c->n_occ, 1) > 0 && n3 % TAU_TB == 0 &&
-                   t4 <= 0.5 * (double)fr;
+    const bool force_upper = lay && std::strcmp(lay, "upper") == 0;
+    const bool tiled = n3 % TAU_TB == 0;
+    const double t4 = (double)c->n_ent * 4.0 * (double)n3 * sizeof(T);
+    c->tau_entry = c->tau_sym = false;
+    if (!force_pair && !force_upper && tiled && k1d_default_variant<T>(c->n_occ, 1) > 0 && t4 <= half) {
+      c->tau_entry = true;
+    } else if (!force_pair && tiled && k1d_sym_default_variant<T>(c->n_occ, 1) > 0) {
+      CA(build_sym_lists(c, pid));
+      c->tau_sym = (double)c->n_ent_u * 4.0 * (double)n3 * sizeof(T) <= half;
+    }
     if (c->tau_entry) {
       CA(dalloc(c, &tau, (size_t)c->n_ent * 4 * n3));
+    } else if (c->tau_sym) {
+      CA(dalloc(c, &tau, (size_t)c->n_ent_u * 4 * n3));
     } else {
       CA(dalloc(c, &tau, (size_t)c->n_pairs * n3));
     }
     CK(cudaStreamSynchronize(c->st));   // the allocation is visible in the next context's free memory
   }
   if (c->tau_entry) CK(cudaMemsetAsync(tau, 0, sizeof(T) * (size_t)c->n_ent * 4 * n3, c->st));
+  if (c->tau_sym) CK(cudaMemsetAsync(tau, 0, sizeof(T) * (size_t)c->n_ent_u * 4 * n3, c->st));
   c->tau = tau;
   const size_t budget = (size_t)2 << 30;
   long nb = (long)(budget / (n3 * sizeof(cplx<T>))) * 2;
@@ -780,6 +937,7 @@ int build_tau_impl(bse_ctx* c) {
     CK(grid_coulomb<T>(grids, ng, c->N, c->L, c->omega, 1, 1.0, c->st));
     CK(fft3d<T>(grids, ng, c->N, +1, tw_of<T>(c), c->st));
     if (c->tau_entry) CK(scatter_tau4<T>(b, grids, n3, p0, c->tslot, c->n_ent, tau, c->st));
+    else if (c->tau_sym) CK(scatter_tau4<T>(b, grids, n3, p0, c->uslot, c->n_ent_u, tau, c->st));
     else CK(deinterleave_pairs<T>(b, grids, n3, p0, c->n_pairs, tau, c->st));
   }
   CK(cudaStreamSynchronize(c->st));
@@ -2158,6 +2316,9 @@ int apply_static_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out, unsigned 
     CK(k1d_tiled<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, c->n_ent, c->bptr, c->bw,
                     c->n_rblocks, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr,
                     k1d_variant_for<T>(c, (int)n_vec), c->st));
+  } else if (c->tau_sym) {
+    CK(k1d_sym_tiled<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, k1d_sym_lists(c), vloc_of<T>(c),
+                        (const T*)gh, upsi_of<T>(c), sf, (T*)gr, k1d_sym_variant_for<T>(c, (int)n_vec), c->st));
   } else {
     CK(k1d_combine<T>((int)n_vec, c->n_occ, n3, (const T*)ga, (const T*)c->tau, c->n_pairs, c->nbr_ptr, c->nbr_w,
                       c->nbr_p, vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, c->st));

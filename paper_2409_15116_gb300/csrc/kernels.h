@@ -151,6 +151,32 @@ cudaError_t jade_round(int K_use, int K, int n, double* A, double* U, const int2
 cudaError_t set_identity(int n, double* U, cudaStream_t st);
 void jade_schedule(int n, std::vector<int2>& pairs, int& rounds, int& per_round);
 
+// ---- k1d_sym.cu (tau stored once per pair) ----
+// Row-block lists of the symmetric-layout K1d kernel (device arrays). Row block b = orbitals
+// 4b..4b+3. Upper entries: for each b, every neighbour w >= 4b of any of b's rows, in
+// increasing w; entry e stores tau_{4b+i, w}, i = 0..3, in the entry-major tau (tau4_off).
+// Transposed tiles: for each b, every earlier block J < b with a pair to b; tile k names J's
+// entries (J, 4b+i) (-1 where absent) and the rows j of J that pair with b.
+struct K1dLists {
+  long n_ent = 0;                 // upper entries
+  int n_blocks = 0;               // ceil(n_occ / 4)
+  const int* bptr = nullptr;      // [n_blocks + 1] upper entries of block b: bptr[b] .. bptr[b+1]
+  const int* bw = nullptr;        // [n_ent] neighbour w of each entry
+  const int* tptr = nullptr;      // [n_blocks + 1] transposed tiles of block b
+  const int* tinfo = nullptr;     // [n_tiles] (J << 4) | (mask of J's rows j that pair with b)
+  const int4* tent = nullptr;     // [n_tiles] entries (J, 4b+i), i = 0..3, -1 where absent
+};
+int k1d_sym_num_variants();
+int k1d_sym_padded_vectors(int n_vec, int variant);
+template <typename T>
+int k1d_sym_default_variant(int n_occ, int n_vec);
+template <typename T>
+bool k1d_sym_fits(int n_occ, int variant);
+template <typename T>
+cudaError_t k1d_sym_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau4, const K1dLists& L,
+                          const T* vloc, const T* vh, const T* upsi, double sf, T* out, int variant,
+                          cudaStream_t st, long n_pts = -1);
+
 // ---- k1d.cu ----
 // tile variants of the K1d kernel, numbered 1 .. k1d_num_variants(); 0 = default for the width
 int k1d_num_variants();

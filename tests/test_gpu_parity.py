@@ -160,6 +160,24 @@ def test_per_pair_tau_untiled_vs_matrix_free(ragged_case, prec, tol, monkeypatch
     assert rel(got, ref) <= tol, rel(got, ref)
 
 
+# tau stored once per pair (the layout for systems whose ordered entry-major tau would not
+# fit), read by the symmetric-layout tiled kernel
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
+def test_once_per_pair_tau_vs_matrix_free(ragged_case, prec, tol, monkeypatch):
+    inst, A, ref = ragged_case
+    monkeypatch.setenv("BSE_TAU_LAYOUT", "upper")
+    c = ctx_for(inst, prec)
+    a = dev(A, prec)
+    out = torch.empty_like(a)
+    c.apply(a, out)
+    got = out.double().cpu().numpy()
+    assert rel(got, ref) <= tol, rel(got, ref)
+    for n in (1, 5):                       # other block widths (own tuned variants)
+        o = torch.empty_like(a[:n])
+        c.apply(a[:n].contiguous(), o)
+        assert rel(o.double().cpu().numpy(), ref[:n]) <= tol
+
+
 @pytest.mark.parametrize("variant", range(1, 14))
 @pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
 def test_k1d_tile_variants_vs_matrix_free(ragged_case, variant, prec, tol, monkeypatch):

@@ -70,8 +70,11 @@ def test_op256_operator_sampled_rows(prec, tol, n_vec):
     assert err <= tol, err
 
 
+@pytest.mark.parametrize("layout", ["", "upper"])
 @pytest.mark.parametrize("prec,tol", [(1, 2e-5), (0, 1e-11)])
-def test_grid72_64_orbitals_every_row(prec, tol):
+def test_grid72_64_orbitals_every_row(prec, tol, layout, monkeypatch):
+    if layout:
+        monkeypatch.setenv("BSE_TAU_LAYOUT", layout)
     inst = make_localized(12, 20.0, 72, 64, 2.5, 128, n_eig=4, block=4)
     err = _run(inst, prec, 5, None, 31)
     assert err <= tol, err
