@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--nvec", type=int, default=32)
     ap.add_argument("--batch", type=int, default=0,
                     help="solve this many uneven systems of the batch family together (bse_solve_batch)")
+    ap.add_argument("--lanczos", type=int, default=0,
+                    help="time a Lanczos absorption chain of this many steps for x, y, z (bse_lanczos)")
     ap.add_argument("--no-batch-line", action="store_true",
                     help="skip the 64-system batched solve that the default line reports under 'batch'")
     return ap.parse_args()
@@ -333,8 +335,10 @@ def main():
                 "l2": "inputs larger than L2 (tau and r-space workspaces exceed 129 MB)"}
     if args.config == "large":
         # one GPU cannot hold a second large context (e2e), the FP64 plain solve (142 GB of tau
-        # plus an FP64 subspace) or, on the host, the FP64 oracle's tau (142 GB)
+        # plus an FP64 subspace) or, on the host, the FP64 oracle's tau (142 GB); the r-space
+        # workspace is held to 48 GB (six trial vectors at a time) next to 108 GB of tau
         args.no_e2e = args.no_fp64 = args.no_cpu = args.no_batch_line = True
+        os.environ.setdefault("BSE_WORKSPACE_GB", "48")
 
     if args.impl == "reference":
         if rank != 0:
@@ -372,6 +376,27 @@ def main():
 
     if args.apply_only:
         return apply_only(args, inst, ctx, stream, binding)
+    if args.lanczos:
+        ctx.build_tau()
+        ctx.lanczos(8, dirs=(0, 1, 2))                  # warm-up (tuning of the 3-vector width)
+        torch.cuda.synchronize()
+        ctx.profile(-1)
+        ctx.profile(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        a, b, n2 = ctx.lanczos(args.lanczos, dirs=(0, 1, 2))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.profile(0)
+        prof, _ = ctx.profile_read()
+        om = np.linspace(0.0, 4.0, 2001)
+        g = ctx.lanczos_spectrum(a[0], b[0], n2[0], om, 0.01)
+        print(json.dumps({"mode": "lanczos", "config": args.config, "steps": args.lanczos, "n_pol": 3,
+                          "s": e0.elapsed_time(e1) / 1e3, "ms_per_step": e0.elapsed_time(e1) / args.lanczos,
+                          "spectrum_finite": bool(np.isfinite(g).all()),
+                          "regions_ms": {k: v["ms"] for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}}),
+              flush=True)
+        return
     if args.batch:
         return batch_mode(args, binding, Context, PREC_MIXED, PREC_FP64)
 

@@ -148,6 +148,7 @@ struct bse_ctx {
   // tau stored once per pair for the symmetric-layout tiled kernel (when the entry-major one
   // would not fit): upper entries and transposed tiles of every row block
   bool tau_sym = false;
+  int tau_layout = -1;       // layout taken by the first build (0 per pair, 1 entry-major, 2 once per pair)
   int *ubptr = nullptr, *ubw = nullptr, *utptr = nullptr, *utinfo = nullptr;
   int4* utent = nullptr;
   int2* uslot = nullptr;
@@ -860,9 +861,11 @@ int build_tau_impl(bse_ctx* c) {
   // BSE_TAU_LAYOUT=pair forces the per-pair layout and the untiled kernel.
   // Layout: the ordered entry-major tau where it takes at most half of the free memory, else
   // the symmetric one (each pair once) where that fits, else the per-pair layout with the
-  // untiled kernel; BSE_TAU_LAYOUT=upper or pair skips the earlier choices. Contexts that
-  // build tau at the same time (bse_solve_batch) take the decision and the allocation one
-  // after another, so each sees the memory the earlier ones took.
+  // untiled kernel; BSE_TAU_LAYOUT=upper or pair skips the earlier choices. The first build of
+  // a context decides and later builds keep that layout (their free memory no longer shows
+  // what the context itself holds, e.g. blocks a caching allocator keeps for it). Contexts
+  // that build tau at the same time (bse_solve_batch) take the decision and the allocation
+  // one after another, so each sees the memory the earlier ones took.
   T* tau;
   {
     std::lock_guard<std::mutex> lk(g_tau_layout_mu);
@@ -875,11 +878,19 @@ int build_tau_impl(bse_ctx* c) {
     const bool tiled = n3 % TAU_TB == 0;
     const double t4 = (double)c->n_ent * 4.0 * (double)n3 * sizeof(T);
     c->tau_entry = c->tau_sym = false;
-    if (!force_pair && !force_upper && tiled && k1d_default_variant<T>(c->n_occ, 1) > 0 && t4 <= half) {
+    if (c->tau_layout == 1) {
       c->tau_entry = true;
-    } else if (!force_pair && tiled && k1d_sym_default_variant<T>(c->n_occ, 1) > 0) {
+    } else if (c->tau_layout == 2) {
       CA(build_sym_lists(c, pid));
-      c->tau_sym = (double)c->n_ent_u * 4.0 * (double)n3 * sizeof(T) <= half;
+      c->tau_sym = true;
+    } else if (c->tau_layout < 0) {
+      if (!force_pair && !force_upper && tiled && k1d_default_variant<T>(c->n_occ, 1) > 0 && t4 <= half) {
+        c->tau_entry = true;
+      } else if (!force_pair && tiled && k1d_sym_default_variant<T>(c->n_occ, 1) > 0) {
+        CA(build_sym_lists(c, pid));
+        c->tau_sym = (double)c->n_ent_u * 4.0 * (double)n3 * sizeof(T) <= half;
+      }
+      c->tau_layout = c->tau_entry ? 1 : (c->tau_sym ? 2 : 0);
     }
     if (c->tau_entry) {
       CA(dalloc(c, &tau, (size_t)c->n_ent * 4 * n3));
