@@ -141,13 +141,26 @@ __device__ __forceinline__ void ld_tau4(T (&tv)[4], const T* p) {
   }
 }
 
-// CTAs per SM the register budget is sized for: two of 256 threads, one of 512, and one for
-// the wide vector chunks (SC >= 12), whose a(r) stage leaves room for one CTA anyway
+// CTAs per SM the register budget is sized for by default: two of 256 threads, one of 512,
+// and one for the wide vector chunks (SC >= 12), whose accumulators want more than 128
+// registers. Variant 14 holds 12-vector chunks to two CTAs per SM (two 96 KB a(r) stages fit):
+// twice the tau loads in flight per SM, 8.1 against 10.4 ms for 12 vectors on the 72^3 x 256
+// workload, where the kernel is bound by the loads in flight rather than by instructions
 template <int SC, int NT>
 constexpr int k1d_min_blocks() { return SC >= 12 ? 1 : 512 / NT; }
 
-template <typename T, int TR, int SC, int NT>
-__global__ void __launch_bounds__(NT, k1d_min_blocks<SC, NT>()) k1d_tile_kernel(
+// L2 prefetch of a byte range (16-byte aligned start, size a multiple of 16): no registers
+// or shared memory are held while the data moves
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  if (bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// PF: the first CTA of each 32-point tau tile (first vector chunk) asks L2 for a group's
+// next row block of tau (the whole tile's stretch of it) while the group works on the
+// current one, and for the first block while a(r) is staged; the other CTAs of the tile and
+// the other vector chunks then find it in L2
+template <typename T, int TR, int SC, int NT, int MINB, bool PF = false>
+__global__ void __launch_bounds__(NT, MINB) k1d_tile_kernel(
     int n_vec, int n_occ, long n3, const T* __restrict__ a, const T* __restrict__ tau4, long n_ent,
     const int* __restrict__ bptr, const int* __restrict__ bw, int n_blocks, const T* __restrict__ vloc,
     const T* __restrict__ vh, const T* __restrict__ upsi, T sf, T* __restrict__ out) {
@@ -166,6 +179,13 @@ __global__ void __launch_bounds__(NT, k1d_min_blocks<SC, NT>()) k1d_tile_kernel(
   const int t = tid % TR, g = tid / TR;
   constexpr int G = NT / TR;
   const long r = r0 + t;
+  const bool leader = PF && t == 0 && chunk == 0 && (r0 % TAU_TB) == 0;
+  const T* tau_tile = tau4 + tau4_off(0, r0 - r0 % TAU_TB, n_ent);
+  auto prefetch_block = [&](int b) {
+    const int f0 = __ldg(bptr + b), f1 = __ldg(bptr + b + 1);
+    prefetch_l2(tau_tile + (size_t)f0 * 4 * TAU_TB, (unsigned)(f1 - f0) * 4u * TAU_TB * (unsigned)sizeof(T));
+  };
+  if (leader && g < n_blocks) prefetch_block(g);
   // stage a(field (s0+s, w), r0+t) in layout order, so the lanes of a warp fill
   // consecutive shared-memory words
   {
@@ -186,6 +206,7 @@ __global__ void __launch_bounds__(NT, k1d_min_blocks<SC, NT>()) k1d_tile_kernel(
   const T* tau_r = tau4 + tau4_off(0, r, n_ent);     // entry e at tau_r[e * 4 TAU_TB]
   const unsigned gmask = (TR == 32) ? 0xffffffffu : (((1u << TR) - 1u) << ((tid & 31) & ~(TR - 1)));
   for (int rb = g; rb < n_blocks; rb += G) {
+    if (leader && rb + G < n_blocks) prefetch_block(rb + G);
     RowAcc<T, SC> acc;
     acc.zero();
     const int e0 = bptr[rb], e1 = bptr[rb + 1];
@@ -249,7 +270,8 @@ struct Variant { int tr, sc, nt; };
 constexpr Variant kVariants[] = {{0, 0, 0},     {16, 8, 512}, {8, 8, 256},  {16, 4, 256},
                                  {8, 4, 256},   {16, 2, 256}, {16, 1, 256}, {16, 8, 256},
                                  {8, 8, 512},   {32, 4, 512}, {32, 8, 512}, {32, 2, 256},
-                                 {8, 12, 256},  {8, 16, 256}};
+                                 {8, 12, 256},  {8, 16, 256}, {8, 12, 256}, {8, 12, 256},
+                                 {8, 8, 256},   {8, 4, 256}};
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0])) - 1;
 
 template <typename T>
@@ -258,7 +280,7 @@ size_t variant_smem(int n_occ, int v) {
   return ((size_t)n_occ * q.tr * q.sc + (size_t)q.tr * q.sc) * sizeof(T);
 }
 
-template <typename T, int TR, int SC, int NT>
+template <typename T, int TR, int SC, int NT, int MINB = k1d_min_blocks<SC, NT>(), bool PF = false>
 cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T* tau4, long n_ent, const int* bptr,
                        const int* bw, int n_blocks, const T* vloc, const T* vh,
                        const T* upsi, double sf, T* out, long n_pts, cudaStream_t st) {
@@ -270,12 +292,12 @@ cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T* tau4,
     static std::once_flag once;
     static cudaError_t once_st = cudaSuccess;
     cudaError_t e0 = once_status(once, once_st, [&] {
-      return cudaFuncSetAttribute(k1d_tile_kernel<T, TR, SC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      return cudaFuncSetAttribute(k1d_tile_kernel<T, TR, SC, NT, MINB, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)K1D_SMEM_MAX);
     });
     if (e0 != cudaSuccess) return e0;
     const long blocks = (n_pts / TR) * ((n_vec + SC - 1) / SC);
-    k1d_tile_kernel<T, TR, SC, NT><<<(unsigned)blocks, NT, smem, st>>>(
+    k1d_tile_kernel<T, TR, SC, NT, MINB, PF><<<(unsigned)blocks, NT, smem, st>>>(
         n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi, (T)sf, out);
     note_launch();
     return cudaGetLastError();
@@ -346,6 +368,19 @@ cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau4, 
     BSE_K1D_CASE(11, 32, 2, 256)
     BSE_K1D_CASE(12, 8, 12, 256)
     BSE_K1D_CASE(13, 8, 16, 256)
+    case 14:   // 12-vector chunks held to the register budget of two CTAs per SM
+      return launch_k1d<T, 8, 12, 256, 2>(n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi, sf,
+                                          out, n_pts, st);
+    // the same tile shapes with the L2 prefetch of the next row block
+    case 15:
+      return launch_k1d<T, 8, 12, 256, 2, true>(n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi,
+                                                sf, out, n_pts, st);
+    case 16:
+      return launch_k1d<T, 8, 8, 256, 2, true>(n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi,
+                                               sf, out, n_pts, st);
+    case 17:
+      return launch_k1d<T, 8, 4, 256, 2, true>(n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi,
+                                               sf, out, n_pts, st);
     default: return cudaErrorInvalidValue;
   }
 #undef BSE_K1D_CASE
