@@ -14,7 +14,10 @@
 // part = odd field); they separate again through Hermitian symmetry at the sphere.
 #include "common.cuh"
 #include "kernels.h"
+
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <vector>
 
@@ -435,17 +438,38 @@ __device__ __forceinline__ void pstage(int Ns, int sign, int n_lines, const C* t
 }
 
 template <typename T, int N>
-constexpr size_t plane_smem() {
+constexpr size_t plane_smem_base() {
   // column buffer A [NX <= N/2 + 1 slots] + (column buffer B | row plane P) + twiddles + slots
   constexpr int NXM = N / 2 + 1;
   return (size_t)(NXM * PPad<N>::LS + N * PPad<N>::LS + N) * sizeof(cplx<T>) + (size_t)N * sizeof(int);
 }
+// plus, for the inverse, the prefetched columns of the next plane (NC values)
+template <typename T, int N>
+size_t plane_smem(bool inverse, int NC) {
+  return plane_smem_base<T, N>() + (inverse ? (size_t)NC * sizeof(cplx<T>) + 16 : 0);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_all() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_groups() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // inverse: I1[g][z][.] (z-transformed columns) -> grid plane (g, z); forward: the reverse.
 // Column buffers hold the band's x slots as lines over y; the row plane holds lines over x.
+// Persistent: a CTA takes planes gz = blockIdx.x, blockIdx.x + gridDim.x, ... of the n_planes
+// (g, z) planes. Twiddles and x slots are set up once per CTA; in the inverse the next
+// plane's columns are copied (cp.async, 16 bytes per copy where aligned) into a prefetch
+// buffer while the current plane is transformed.
 template <typename T, int N, bool INV>
 __global__ void __launch_bounds__(256) sph_plane_kernel(cplx<T>* __restrict__ I1, cplx<T>* __restrict__ grid,
-                                                       SphereMap m, int sign, const cplx<T>* __restrict__ table) {
+                                                       SphereMap m, int sign, const cplx<T>* __restrict__ table,
+                                                       long n_planes) {
   using C = cplx<T>;
   constexpr int R0 = Plan2<N>::r0, R1 = Plan2<N>::r1;
   constexpr int NXM = N / 2 + 1;
@@ -455,50 +479,69 @@ __global__ void __launch_bounds__(256) sph_plane_kernel(cplx<T>* __restrict__ I1
   C* P = colB;                                       // [N][LS]
   C* tw = P + N * PPad<N>::LS;
   int* slot = reinterpret_cast<int*>(tw + N);        // slot of x in the band, -1 outside
+  C* pre = reinterpret_cast<C*>(smem_raw + ((plane_smem_base<T, N>() + 15) & ~(size_t)15));  // [NC], inverse
   load_twiddles<C, N>(tw, table, sign);
   for (int x = threadIdx.x; x < N; x += blockDim.x) slot[x] = -1;
   __syncthreads();
   for (int l = threadIdx.x; l < m.NX; l += blockDim.x) slot[m.xs[l]] = l;
-  const long gz = blockIdx.x;                        // g * N + z
-  C* I1r = I1 + gz * m.NC;
-  C* Gp = grid + gz * (long)N * N;
   const int nx = m.NX;
-  if (INV) {
-    for (int e = threadIdx.x; e < nx * PPad<N>::LS; e += blockDim.x) colA[e] = cmk<C>(0, 0);
-    __syncthreads();
-    for (int c = threadIdx.x; c < m.NC; c += blockDim.x) colA[lidx<N>(m.cxi[c], m.cy[c])] = I1r[c];
-    __syncthreads();
-    // y lines of the band: A -> B -> A
-    pstage<C, N, R0, true>(1, sign, nx, tw, [&](int l, int q) { return colA[lidx<N>(l, q)]; },
-                           [&](int l, int q, C v) { colB[lidx<N>(l, q)] = v; });
-    __syncthreads();
-    pstage<C, N, R1, true>(R0, sign, nx, tw, [&](int l, int q) { return colB[lidx<N>(l, q)]; },
-                           [&](int l, int q, C v) { colA[lidx<N>(l, q)] = v; });
-    __syncthreads();
-    // x lines: the first stage reads the band from the column buffer (zero outside it),
-    // the second writes the plane to global memory
-    pstage<C, N, R0, true>(1, sign, N, tw,
-                           [&](int y, int x) { const int s = slot[x]; return s >= 0 ? colA[lidx<N>(s, y)] : cmk<C>(0, 0); },
-                           [&](int y, int x, C v) { P[lidx<N>(y, x)] = v; });
-    __syncthreads();
-    pstage<C, N, R1, false>(R0, sign, N, tw, [&](int y, int x) { return P[lidx<N>(y, x)]; },
-                            [&](int y, int x, C v) { Gp[y * N + x] = v; });
-  } else {
-    // x lines: the first stage reads the plane from global memory, the second keeps the band
-    pstage<C, N, R0, false>(1, sign, N, tw, [&](int y, int x) { return Gp[y * N + x]; },
-                            [&](int y, int x, C v) { P[lidx<N>(y, x)] = v; });
-    __syncthreads();
-    pstage<C, N, R1, true>(R0, sign, N, tw, [&](int y, int x) { return P[lidx<N>(y, x)]; },
-                           [&](int y, int x, C v) { const int s = slot[x]; if (s >= 0) colA[lidx<N>(s, y)] = v; });
-    __syncthreads();
-    // y lines of the band: A -> B -> A
-    pstage<C, N, R0, true>(1, sign, nx, tw, [&](int l, int q) { return colA[lidx<N>(l, q)]; },
-                           [&](int l, int q, C v) { colB[lidx<N>(l, q)] = v; });
-    __syncthreads();
-    pstage<C, N, R1, true>(R0, sign, nx, tw, [&](int l, int q) { return colB[lidx<N>(l, q)]; },
-                           [&](int l, int q, C v) { colA[lidx<N>(l, q)] = v; });
-    __syncthreads();
-    for (int c = threadIdx.x; c < m.NC; c += blockDim.x) I1r[c] = colA[lidx<N>(m.cxi[c], m.cy[c])];
+  // the columns of plane gz into the prefetch buffer (16-byte copies when the row is aligned)
+  auto prefetch = [&](long gz) {
+    const C* src = I1 + gz * m.NC;
+    if (sizeof(C) == 8 && (m.NC & 1) == 0) {
+      for (int c = 2 * threadIdx.x; c < m.NC; c += 2 * blockDim.x) cp_async16(pre + c, src + c);
+    } else if (sizeof(C) == 16) {
+      for (int c = threadIdx.x; c < m.NC; c += blockDim.x) cp_async16(pre + c, src + c);
+    } else {
+      for (int c = threadIdx.x; c < m.NC; c += blockDim.x) cp_async8(pre + c, src + c);
+    }
+    cp_async_commit_all();
+  };
+  long gz = blockIdx.x;
+  if (INV && gz < n_planes) prefetch(gz);
+  for (; gz < n_planes; gz += gridDim.x) {
+    C* I1r = I1 + gz * m.NC;
+    C* Gp = grid + gz * (long)N * N;
+    if (INV) {
+      for (int e = threadIdx.x; e < nx * PPad<N>::LS; e += blockDim.x) colA[e] = cmk<C>(0, 0);
+      cp_async_wait_all_groups();
+      __syncthreads();
+      for (int c = threadIdx.x; c < m.NC; c += blockDim.x) colA[lidx<N>(m.cxi[c], m.cy[c])] = pre[c];
+      __syncthreads();
+      if (gz + gridDim.x < n_planes) prefetch(gz + gridDim.x);
+      // y lines of the band: A -> B -> A
+      pstage<C, N, R0, true>(1, sign, nx, tw, [&](int l, int q) { return colA[lidx<N>(l, q)]; },
+                             [&](int l, int q, C v) { colB[lidx<N>(l, q)] = v; });
+      __syncthreads();
+      pstage<C, N, R1, true>(R0, sign, nx, tw, [&](int l, int q) { return colB[lidx<N>(l, q)]; },
+                             [&](int l, int q, C v) { colA[lidx<N>(l, q)] = v; });
+      __syncthreads();
+      // x lines: the first stage reads the band from the column buffer (zero outside it),
+      // the second writes the plane to global memory
+      pstage<C, N, R0, true>(1, sign, N, tw,
+                             [&](int y, int x) { const int s = slot[x]; return s >= 0 ? colA[lidx<N>(s, y)] : cmk<C>(0, 0); },
+                             [&](int y, int x, C v) { P[lidx<N>(y, x)] = v; });
+      __syncthreads();
+      pstage<C, N, R1, false>(R0, sign, N, tw, [&](int y, int x) { return P[lidx<N>(y, x)]; },
+                              [&](int y, int x, C v) { Gp[y * N + x] = v; });
+    } else {
+      __syncthreads();                                // the previous plane's gather is done with colA
+      // x lines: the first stage reads the plane from global memory, the second keeps the band
+      pstage<C, N, R0, false>(1, sign, N, tw, [&](int y, int x) { return Gp[y * N + x]; },
+                              [&](int y, int x, C v) { P[lidx<N>(y, x)] = v; });
+      __syncthreads();
+      pstage<C, N, R1, true>(R0, sign, N, tw, [&](int y, int x) { return P[lidx<N>(y, x)]; },
+                             [&](int y, int x, C v) { const int s = slot[x]; if (s >= 0) colA[lidx<N>(s, y)] = v; });
+      __syncthreads();
+      // y lines of the band: A -> B -> A
+      pstage<C, N, R0, true>(1, sign, nx, tw, [&](int l, int q) { return colA[lidx<N>(l, q)]; },
+                             [&](int l, int q, C v) { colB[lidx<N>(l, q)] = v; });
+      __syncthreads();
+      pstage<C, N, R1, true>(R0, sign, nx, tw, [&](int l, int q) { return colB[lidx<N>(l, q)]; },
+                             [&](int l, int q, C v) { colA[lidx<N>(l, q)] = v; });
+      __syncthreads();
+      for (int c = threadIdx.x; c < m.NC; c += blockDim.x) I1r[c] = colA[lidx<N>(m.cxi[c], m.cy[c])];
+    }
   }
 }
 
@@ -507,10 +550,11 @@ static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>*
                                  long n_grids, const SphereMap& m, const cplx<T>* table, cudaStream_t st) {
   constexpr int TL = Plan<N>::TX;
   const size_t smem = (size_t)(2 * TL * Pad<N>::LS + N) * sizeof(cplx<T>);
-  constexpr size_t psmem = plane_smem<T, N>();
-  constexpr bool use_plane = psmem <= 220 * 1024;
+  const size_t psmem = plane_smem<T, N>(inverse, m.NC);
+  constexpr bool use_plane = plane_smem_base<T, N>() <= 200 * 1024;
   static std::once_flag once;
   static cudaError_t once_st = cudaSuccess;
+  static int n_sm = 0;
   cudaError_t e0 = once_status(once, once_st, [&] {
     cudaError_t e = cudaSuccess;
     const void* ks[6] = {(const void*)sph_z_kernel<T, N, true>, (const void*)sph_z_kernel<T, N, false>,
@@ -520,13 +564,41 @@ static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>*
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if constexpr (use_plane) {
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sph_plane_kernel<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+        e = cudaFuncSetAttribute(sph_plane_kernel<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sph_plane_kernel<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+        e = cudaFuncSetAttribute(sph_plane_kernel<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    }
+    if (e == cudaSuccess) {
+      int dev = 0;
+      e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     }
     return e;
   });
   if (e0 != cudaSuccess) return e0;
+  // persistent plane kernels: as many CTAs as fit on the device at this shared-memory size
+  long plane_grid = 0;
+  if constexpr (use_plane) {
+    if (psmem > 220 * 1024) return cudaErrorInvalidValue;
+    int occ = 0;
+    static std::mutex mu;
+    static std::map<std::pair<bool, size_t>, int> occ_of;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      auto it = occ_of.find(std::make_pair(inverse, psmem));
+      if (it == occ_of.end()) {
+        cudaError_t e = inverse
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sph_plane_kernel<T, N, true>, 256, psmem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sph_plane_kernel<T, N, false>, 256, psmem);
+        if (e != cudaSuccess) return e;
+        occ_of[std::make_pair(inverse, psmem)] = occ;
+      } else {
+        occ = it->second;
+      }
+    }
+    if (occ < 1) return cudaErrorInvalidValue;
+    plane_grid = std::min<long>(n_grids * N, (long)occ * n_sm);
+  }
   if (n_grids <= 0) return cudaSuccess;
   const long bz = n_grids * ((m.NC + TL - 1) / TL);
   const long by = n_grids * N * ((m.NX + TL - 1) / TL);
@@ -535,14 +607,16 @@ static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>*
   if (inverse) {
     sph_z_kernel<T, N, true><<<(unsigned)bz, 256, smem, st>>>(S, I1, m, +1, table); note_launch();
     if constexpr (use_plane) {
-      sph_plane_kernel<T, N, true><<<(unsigned)bp, 256, psmem, st>>>(I1, grid, m, +1, table); note_launch();
+      sph_plane_kernel<T, N, true><<<(unsigned)plane_grid, 256, psmem, st>>>(I1, grid, m, +1, table, bp);
+      note_launch();
     } else {
       sph_y_kernel<T, N, true><<<(unsigned)by, 256, smem, st>>>(I1, I2, m, +1, table); note_launch();
       sph_x_kernel<T, N, true><<<(unsigned)bx, 256, smem, st>>>(I2, grid, m, +1, table); note_launch();
     }
   } else {
     if constexpr (use_plane) {
-      sph_plane_kernel<T, N, false><<<(unsigned)bp, 256, psmem, st>>>(I1, grid, m, -1, table); note_launch();
+      sph_plane_kernel<T, N, false><<<(unsigned)plane_grid, 256, psmem, st>>>(I1, grid, m, -1, table, bp);
+      note_launch();
     } else {
       sph_x_kernel<T, N, false><<<(unsigned)bx, 256, smem, st>>>(I2, grid, m, -1, table); note_launch();
       sph_y_kernel<T, N, false><<<(unsigned)by, 256, smem, st>>>(I1, I2, m, -1, table); note_launch();
