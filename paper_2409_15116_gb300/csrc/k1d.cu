@@ -18,7 +18,9 @@
 //    without that neighbour) and only the neighbour index w is broadcast in the group;
 //  * tau values go straight from global memory to registers through a ring of PD entries,
 //    so PD entries of loads are in flight per lane while the oldest one is consumed; tau is
-//    point-tiled, so the tau a CTA reads is one contiguous stretch of memory;
+//    point-tiled, so the tau a CTA reads is one contiguous stretch of memory (the ring
+//    variants keep the entries in flight in shared memory instead, by cp.async, which frees
+//    the registers: k1d_ring_kernel);
 //  * each tau value feeds SC multiply-adds and each staged a value four, accumulated in
 //    packed FP32x2 FMAs for single precision.
 #include "common.cuh"
@@ -265,19 +267,153 @@ __global__ void __launch_bounds__(NT, MINB) k1d_tile_kernel(
   }
 }
 
+// The same product with tau streamed through a shared-memory ring (RING variants): each
+// group keeps D entries of tau in flight as 16-byte cp.async copies (no registers held), one
+// copy per lane per entry, and reads each entry back with one 16-byte shared load when it
+// is consumed. A lane refills the slot of entry e + D right after consuming entry e; one
+// commit group per entry keeps the per-thread wait (cp.async.wait_group D-1) exact. The
+// neighbour index of an entry is broadcast in the group when the entry is consumed.
+template <int D>
+__device__ __forceinline__ void cp_async_wait_ring() { asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 1) : "memory"); }
+__device__ __forceinline__ void cp_async_commit_one() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async16_cg(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+template <int TR, int SC, int NT, int D>
+__global__ void __launch_bounds__(NT, 2) k1d_ring_kernel(
+    int n_vec, int n_occ, long n3, const float* __restrict__ a, const float* __restrict__ tau4, long n_ent,
+    const int* __restrict__ bptr, const int* __restrict__ bw, int n_blocks, const float* __restrict__ vloc,
+    const float* __restrict__ vh, const float* __restrict__ upsi, float sf, float* __restrict__ out) {
+  using T = float;
+  extern __shared__ __align__(16) unsigned char k1d_ring_smem[];
+  constexpr int G = NT / TR;
+  T* A = reinterpret_cast<T*>(k1d_ring_smem);        // [n_occ][SC / CH][TR][CH]
+  T* VH = A + (size_t)n_occ * TR * SC;                // [TR][SC]
+  float4* RING = reinterpret_cast<float4*>(VH + TR * SC + 4 - (TR * SC) % 4);  // [G][D][TR]
+  const int n_sc = (n_vec + SC - 1) / SC;
+  const int chunk = blockIdx.x % n_sc;
+  const long r0 = (long)(blockIdx.x / n_sc) * TR;
+  const int s0 = chunk * SC;
+  const int ns = min(SC, n_vec - s0);
+  const int tid = threadIdx.x;
+  const int t = tid % TR, g = tid / TR;
+  const long r = r0 + t;
+  {
+    using L = ALayout<T, SC>;
+    const int n_items = n_occ * TR * SC;
+    for (int it = tid; it < n_items; it += NT) {
+      const int q = it % L::CH, tt = (it / L::CH) % TR, c = (it / (L::CH * TR)) % L::NCH;
+      const int w = it / (SC * TR);
+      const int s = c * L::CH + q;
+      if (s < ns) cp_async<4>(A + it, a + pair_off<T>((long)(s0 + s) * n_occ + w, r0 + tt, n3));
+    }
+  }
+  cp_async_commit_one();
+  if (g < SC) VH[t * SC + g] = (g < ns) ? vh[pair_off<T>(s0 + g, r, n3)] : (T)0;
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  const T vl = vloc[r];
+  const T* tau_r = tau4 + tau4_off(0, r, n_ent);
+  float4* ring = RING + (size_t)g * D * TR + t;       // slot k at ring[k * TR]
+  const unsigned gmask = (TR == 32) ? 0xffffffffu : (((1u << TR) - 1u) << ((tid & 31) & ~(TR - 1)));
+  for (int rb = g; rb < n_blocks; rb += G) {
+    RowAcc<T, SC> acc;
+    acc.zero();
+    const int e0 = bptr[rb], e1 = bptr[rb + 1];
+    auto ld_w = [&](int base) { const int e = base + t; return (e < e1) ? bw[e] : 0; };
+    int wA = ld_w(e0), wB = ld_w(e0 + TR);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      if (e0 + k < e1) cp_async16_cg(ring + k * TR, tau_r + (size_t)(e0 + k) * (4 * TAU_TB));
+      cp_async_commit_one();
+    }
+    int slot = 0;
+    for (int base = e0; base < e1; base += TR) {
+      const int wC = ld_w(base + 2 * TR);
+#pragma unroll
+      for (int d = 0; d < TR; ++d) {
+        const int e = base + d;
+        if (e >= e1) break;
+        const int w = gshfl<TR>(gmask, wA, d);
+        cp_async_wait_ring<D>();
+        const float4 q = ring[slot * TR];
+        const T tv[4] = {q.x, q.y, q.z, q.w};
+        T av[SC];
+        lds_a<T, SC, TR>(av, A, w, t);
+        acc.mac(tv, av);
+        // the slot is free once this lane has read it (each lane reads only its own copy)
+        if (e + D < e1) cp_async16_cg(ring + slot * TR, tau_r + (size_t)(e + D) * (4 * TAU_TB));
+        cp_async_commit_one();
+        slot = (slot + 1 == D) ? 0 : slot + 1;
+      }
+      wA = wB;
+      wB = wC;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int v = 4 * rb + i;
+      if (v >= n_occ) break;
+      const T up = sf * upsi[pair_off<T>(v, r, n3)];
+      T av[SC], hv[SC];
+      lds_a<T, SC, TR>(av, A, v, t);
+      lds_vec<T, SC>(hv, VH + t * SC);
+#pragma unroll
+      for (int s = 0; s < SC; ++s) {
+        if (s >= ns) break;
+        const long f = (long)(s0 + s) * n_occ + v;
+        out[pair_off<T>(f, r, n3)] = vl * av[s] + hv[s] * up - acc.get(i, s);
+      }
+    }
+  }
+}
+
+template <typename T, int TR, int SC, int NT, int D>
+cudaError_t launch_ring(int n_vec, int n_occ, long n3, const T* a, const T* tau4, long n_ent, const int* bptr,
+                        const int* bw, int n_blocks, const T* vloc, const T* vh, const T* upsi, double sf, T* out,
+                        long n_pts, cudaStream_t st) {
+  if constexpr (sizeof(T) != 4) {
+    return cudaErrorInvalidValue;
+  } else {
+    const size_t smem = ((size_t)n_occ * TR * SC + (size_t)TR * SC + 4) * sizeof(T) +
+                        (size_t)(NT / TR) * D * TR * sizeof(float4);
+    static std::once_flag once;
+    static cudaError_t once_st = cudaSuccess;
+    cudaError_t e0 = once_status(once, once_st, [&] {
+      return cudaFuncSetAttribute(k1d_ring_kernel<TR, SC, NT, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)K1D_SMEM_MAX);
+    });
+    if (e0 != cudaSuccess) return e0;
+    if (smem > K1D_SMEM_MAX) return cudaErrorInvalidValue;
+    const long blocks = (n_pts / TR) * ((n_vec + SC - 1) / SC);
+    k1d_ring_kernel<TR, SC, NT, D><<<(unsigned)blocks, NT, smem, st>>>(n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw,
+                                                                        n_blocks, vloc, vh, upsi, (float)sf, out);
+    note_launch();
+    return cudaGetLastError();
+  }
+}
+
 // tile variants: (points per CTA, vectors per CTA, threads per CTA)
 struct Variant { int tr, sc, nt; };
 constexpr Variant kVariants[] = {{0, 0, 0},     {16, 8, 512}, {8, 8, 256},  {16, 4, 256},
                                  {8, 4, 256},   {16, 2, 256}, {16, 1, 256}, {16, 8, 256},
                                  {8, 8, 512},   {32, 4, 512}, {32, 8, 512}, {32, 2, 256},
                                  {8, 12, 256},  {8, 16, 256}, {8, 12, 256}, {8, 12, 256},
-                                 {8, 8, 256},   {8, 4, 256}};
+                                 {8, 8, 256},   {8, 4, 256},
+                                 // shared-memory tau rings (single precision): 18 .. 20
+                                 {8, 8, 256},   {8, 4, 256},  {8, 12, 256}};
+// ring depth of the shared-memory ring variants (0: register ring); each is the depth that
+// measured fastest for its chunk width with two CTAs per SM (deeper rings take shared memory
+// that L1 needs: 8 vectors, depth 12 ran 5-10% slower than depth 8)
+constexpr int ring_depth(int v) { return v == 18 ? 8 : v == 19 ? 16 : v == 20 ? 4 : 0; }
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0])) - 1;
 
 template <typename T>
 size_t variant_smem(int n_occ, int v) {
   const Variant q = kVariants[v];
-  return ((size_t)n_occ * q.tr * q.sc + (size_t)q.tr * q.sc) * sizeof(T);
+  return ((size_t)n_occ * q.tr * q.sc + (size_t)q.tr * q.sc + 4) * sizeof(T) +
+         (size_t)(q.nt / q.tr) * ring_depth(v) * q.tr * 16;
 }
 
 template <typename T, int TR, int SC, int NT, int MINB = k1d_min_blocks<SC, NT>(), bool PF = false>
@@ -313,6 +449,7 @@ template <typename T>
 bool k1d_fits(int n_occ, int v) {
   if (v < 1 || v > kNumVariants) return false;
   if (sizeof(T) == 8 && kVariants[v].sc >= 8) return false;
+  if (sizeof(T) == 8 && ring_depth(v) > 0) return false;
   return variant_smem<T>(n_occ, v) <= K1D_SMEM_MAX;
 }
 
@@ -381,6 +518,9 @@ cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau4, 
     case 17:
       return launch_k1d<T, 8, 4, 256, 2, true>(n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi,
                                                sf, out, n_pts, st);
+    case 18: return launch_ring<T, 8, 8, 256, 8>(n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi, sf, out, n_pts, st);
+    case 19: return launch_ring<T, 8, 4, 256, 16>(n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi, sf, out, n_pts, st);
+    case 20: return launch_ring<T, 8, 12, 256, 4>(n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi, sf, out, n_pts, st);
     default: return cudaErrorInvalidValue;
   }
 #undef BSE_K1D_CASE

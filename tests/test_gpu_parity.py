@@ -178,7 +178,7 @@ def test_once_per_pair_tau_vs_matrix_free(ragged_case, prec, tol, monkeypatch):
         assert rel(o.double().cpu().numpy(), ref[:n]) <= tol
 
 
-@pytest.mark.parametrize("variant", range(1, 18))
+@pytest.mark.parametrize("variant", range(1, 21))
 @pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
 def test_k1d_tile_variants_vs_matrix_free(ragged_case, variant, prec, tol, monkeypatch):
     inst, A, ref = ragged_case
