@@ -157,6 +157,7 @@ struct bse_ctx {
   // K1d tile variant per block width n_vec, chosen by the autotuner (absent: not tuned yet)
   std::map<int, int> k1d_var;
   int k1d_force = 0;         // BSE_K1D_VARIANT: one variant for every width, no tuning
+  int k1d_force_sym = 0;     // BSE_K1D_SYM_VARIANT: the same for tau stored once per pair
   bool autotune = true;
   int64_t n_pairs = 0, nnz = 0;
   void* tau = nullptr;       // entry-major (tau_entry) or per pair, point-tiled
@@ -531,6 +532,7 @@ K1dLists k1d_sym_lists(const bse_ctx* c);
 
 template <typename T>
 int k1d_sym_variant_for(const bse_ctx* c, int nv) {
+  if (c->k1d_force_sym) return c->k1d_force_sym;
   auto it = c->k1d_var_sym.find(nv);
   return it != c->k1d_var_sym.end() ? it->second : k1d_sym_default_variant<T>(c->n_occ, nv);
 }
@@ -631,7 +633,7 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
                         vloc_of<T>(c), (const T*)gh, upsi_of<T>(c), sf, (T*)gr, k1d_variant_for<T>(c, (int)nv),
                         c->st));
       } else if (c->tau_sym) {
-        if (!c->k1d_var_sym.count((int)nv))
+        if (!c->k1d_force_sym && !c->k1d_var_sym.count((int)nv))
           CA(autotune_k1d_sym<T>(c, (int)nv, n3, (const T*)ga, (const T*)gh, (T*)gr, sf));
         CK(k1d_sym_tiled<T>((int)nv, c->n_occ, n3, (const T*)ga, tau, k1d_sym_lists(c), vloc_of<T>(c),
                             (const T*)gh, upsi_of<T>(c), sf, (T*)gr, k1d_sym_variant_for<T>(c, (int)nv), c->st));
@@ -1625,6 +1627,12 @@ int bse_create(const bse_system* s, int precision, bse_alloc_fn alloc_fn, bse_fr
       const int v = atoi(e);
       const bool ok = (precision == BSE_PREC_FP64) ? k1d_fits<double>(s->n_occ, v) : k1d_fits<float>(s->n_occ, v);
       if (ok) c->k1d_force = v;
+    }
+    // BSE_K1D_SYM_VARIANT=v does the same for the kernel of tau stored once per pair
+    if (const char* e = getenv("BSE_K1D_SYM_VARIANT")) {
+      const int v = atoi(e);
+      const bool ok = (precision == BSE_PREC_FP64) ? k1d_sym_fits<double>(s->n_occ, v) : k1d_sym_fits<float>(s->n_occ, v);
+      if (ok) c->k1d_force_sym = v;
     }
     c->ws_budget = std::max<size_t>(bud, 1);
   }

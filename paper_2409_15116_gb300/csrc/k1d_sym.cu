@@ -27,7 +27,7 @@ namespace bse {
 namespace {
 
 constexpr int K1D_PD = 8;                       // tau prefetch depth (entries per lane)
-constexpr size_t K1D_SMEM_MAX = 220 * 1024;     // opt-in dynamic shared memory used at most
+constexpr size_t K1D_SMEM_MAX = 227 * 1024;     // opt-in dynamic shared memory used at most (the limit)
 
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
@@ -191,8 +191,20 @@ __device__ __forceinline__ void prefetch_block(const T* tau_tile, const K1dLists
 template <int SC, int NT>
 constexpr int k1d_min_blocks() { return SC >= 12 ? 1 : 512 / NT; }
 
-template <typename T, int TR, int SC, int NT>
-__global__ void __launch_bounds__(NT, k1d_min_blocks<SC, NT>()) k1d_sym_kernel(
+__device__ __forceinline__ void cp_async16_cg(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_one() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// RD, RT > 0 (single precision): the upper entries (RD of them) and the transposed tiles (RT
+// of them) in flight in per-group shared-memory rings filled by cp.async (16 bytes per lane
+// per entry, one commit group per entry or tile, so cp.async.wait_group RD-1 or RT-1 before a
+// slot is read is exact) instead of registers; absent entries of a tile are zeroed in its slot
+template <typename T, int TR, int SC, int NT, int RD = 0, int RT = 0, int MINB = k1d_min_blocks<SC, NT>()>
+__global__ void __launch_bounds__(NT, MINB) k1d_sym_kernel(
     int n_vec, int n_occ, long n3, const T* __restrict__ a, const T* __restrict__ tau4, K1dLists L,
     const T* __restrict__ vloc, const T* __restrict__ vh, const T* __restrict__ upsi, T sf,
     T* __restrict__ out) {
@@ -238,10 +250,45 @@ __global__ void __launch_bounds__(NT, k1d_min_blocks<SC, NT>()) k1d_sym_kernel(
   __syncthreads();
   const T vl = vloc[r];
   const unsigned gmask = (TR == 32) ? 0xffffffffu : (((1u << TR) - 1u) << ((tid & 31) & ~(TR - 1)));
+  // shared-memory rings: upper entries [G][RD][TR], tiles [G][RT][4][TR] (16 bytes each)
+  float4* ringU = reinterpret_cast<float4*>(VH + TR * SC + 4 - (TR * SC) % 4) + (size_t)g * RD * TR + t;
+  float4* ringT = reinterpret_cast<float4*>(VH + TR * SC + 4 - (TR * SC) % 4) + (size_t)G * RD * TR +
+                  (size_t)g * RT * 4 * TR + t;
   for (int rb = g; rb < n_blocks; rb += G) {
     if (pf && t == 0 && rb + G < n_blocks) prefetch_block<T>(tau_tile, L, rb + G);
     RowAcc<T, SC> acc;
     acc.zero();
+    if constexpr (RD > 0 && sizeof(T) == 4) {
+      const int e0 = __ldg(L.bptr + rb), e1 = __ldg(L.bptr + rb + 1);
+      auto ld_w = [&](int base) { const int e = base + t; return (e < e1) ? __ldg(L.bw + e) : 0; };
+      int wA = ld_w(e0), wB = ld_w(e0 + TR);
+#pragma unroll
+      for (int k = 0; k < RD; ++k) {
+        if (e0 + k < e1) cp_async16_cg(ringU + k * TR, tau_r + (size_t)(e0 + k) * (4 * TAU_TB));
+        cp_async_commit_one();
+      }
+      int slot = 0;
+      for (int base = e0; base < e1; base += TR) {
+        const int wC = ld_w(base + 2 * TR);
+#pragma unroll
+        for (int d = 0; d < TR; ++d) {
+          const int e = base + d;
+          if (e >= e1) break;
+          const int w = gshfl<TR>(gmask, wA, d);
+          cp_async_wait_n<RD - 1>();
+          const float4 q = ringU[slot * TR];
+          const T tv[4] = {q.x, q.y, q.z, q.w};
+          T av[SC];
+          lds_a<T, SC, TR>(av, A, w, t);
+          acc.mac(tv, av);
+          if (e + RD < e1) cp_async16_cg(ringU + slot * TR, tau_r + (size_t)(e + RD) * (4 * TAU_TB));
+          cp_async_commit_one();
+          slot = (slot + 1 == RD) ? 0 : slot + 1;
+        }
+        wA = wB;
+        wB = wC;
+      }
+    } else
     // ---- upper entries (w >= 4 rb): tau_{4rb+i, w} from one 16-byte load ----
     {
       const int e0 = __ldg(L.bptr + rb), e1 = __ldg(L.bptr + rb + 1);
@@ -276,6 +323,51 @@ __global__ void __launch_bounds__(NT, k1d_min_blocks<SC, NT>()) k1d_sym_kernel(
         wB = wC;
       }
     }
+    if constexpr (RT > 0 && sizeof(T) == 4) {
+      const int k0 = __ldg(L.tptr + rb), k1 = __ldg(L.tptr + rb + 1);
+      int tinf[RT];
+      auto issue_tile = [&](int k, int h) {
+        if (k < k1) {
+          const int4 q = __ldg(L.tent + k);
+          tinf[h] = __ldg(L.tinfo + k);
+          const int qi[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            float4* dst = ringT + (h * 4 + i) * TR;
+            if (qi[i] >= 0) cp_async16_cg(dst, tau_r + (size_t)qi[i] * (4 * TAU_TB));
+            else *dst = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        } else {
+          tinf[h] = 0;
+        }
+        cp_async_commit_one();
+      };
+#pragma unroll
+      for (int h = 0; h < RT; ++h) issue_tile(k0 + h, h);
+      for (int k = k0; k < k1; k += RT) {
+#pragma unroll
+        for (int h = 0; h < RT; ++h) {
+          if (k + h >= k1) break;
+          cp_async_wait_n<RT - 1>();
+          float tt[4][4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float4 q = ringT[(h * 4 + i) * TR];
+            tt[i][0] = q.x; tt[i][1] = q.y; tt[i][2] = q.z; tt[i][3] = q.w;
+          }
+          const int J = tinf[h] >> 4, jm = tinf[h] & 15;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (!((jm >> j) & 1)) continue;
+            T av[SC];
+            lds_a<T, SC, TR>(av, A, 4 * J + j, t);
+            const T cv[4] = {tt[0][j], tt[1][j], tt[2][j], tt[3][j]};
+            acc.mac(cv, av);
+          }
+          issue_tile(k + h + RT, h);
+        }
+      }
+    } else
     // ---- transposed tiles of earlier blocks J < rb: tau_{4J+j, 4rb+i} from J's entries
     // (J, 4rb+i); each of J's rows j that has a pair with rb is one step ----
     {
@@ -322,35 +414,41 @@ __global__ void __launch_bounds__(NT, k1d_min_blocks<SC, NT>()) k1d_sym_kernel(
 }
 
 // tile variants: (points per CTA, vectors per CTA, threads per CTA)
-struct Variant { int tr, sc, nt; };
-constexpr Variant kVariants[] = {{0, 0, 0},     {8, 4, 256},  {8, 8, 256},  {8, 12, 256}, {8, 16, 256},
-                                 {16, 4, 256},  {16, 8, 256}, {16, 8, 512}, {8, 8, 512},  {16, 2, 256},
-                                 {16, 1, 256},  {32, 4, 512}, {32, 2, 256}};
+struct Variant { int tr, sc, nt, rd, rt; };
+constexpr Variant kVariants[] = {{0, 0, 0, 0, 0},    {8, 4, 256, 0, 0},  {8, 8, 256, 0, 0},  {8, 12, 256, 0, 0},
+                                 {8, 16, 256, 0, 0}, {16, 4, 256, 0, 0}, {16, 8, 256, 0, 0}, {16, 8, 512, 0, 0},
+                                 {8, 8, 512, 0, 0},  {16, 2, 256, 0, 0}, {16, 1, 256, 0, 0}, {32, 4, 512, 0, 0},
+                                 {32, 2, 256, 0, 0},
+                                 // shared-memory rings (single precision): upper depth, tiles in flight
+                                 {8, 4, 256, 12, 3}, {8, 4, 256, 8, 4},  {8, 2, 256, 8, 1},  {8, 8, 256, 8, 2},
+                                 {8, 4, 256, 16, 2}, {8, 2, 256, 4, 2},  {16, 2, 256, 8, 1}};
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0])) - 1;
 
 template <typename T>
 size_t variant_smem(int n_occ, int v) {
   const Variant q = kVariants[v];
-  return ((size_t)n_occ * q.tr * q.sc + (size_t)q.tr * q.sc) * sizeof(T);
+  return ((size_t)n_occ * q.tr * q.sc + (size_t)q.tr * q.sc + 4) * sizeof(T) +
+         (size_t)(q.nt / q.tr) * (q.rd + 4 * q.rt) * q.tr * 16;
 }
 
-template <typename T, int TR, int SC, int NT>
+template <typename T, int TR, int SC, int NT, int RD = 0, int RT = 0>
 cudaError_t launch_k1d(int n_vec, int n_occ, long n3, const T* a, const T* tau4, const K1dLists& L,
                        const T* vloc, const T* vh, const T* upsi, double sf, T* out, long n_pts, cudaStream_t st) {
   static_assert(NT % TR == 0 && 32 % TR == 0 && NT / TR >= SC, "tile shape");
-  if constexpr (sizeof(T) == 8 && SC >= 8) {
-    return cudaErrorInvalidValue;   // 4 x SC double accumulators per lane do not fit the register budget
+  if constexpr (sizeof(T) == 8 && (SC >= 8 || RD > 0 || RT > 0)) {
+    return cudaErrorInvalidValue;   // double accumulators do not fit; the rings are single precision
   } else {
-    const size_t smem = ((size_t)n_occ * TR * SC + (size_t)TR * SC) * sizeof(T);
+    const size_t smem = ((size_t)n_occ * TR * SC + (size_t)TR * SC + 4) * sizeof(T) +
+                        (size_t)(NT / TR) * (RD + 4 * RT) * TR * 16;
     static std::once_flag once;
     static cudaError_t once_st = cudaSuccess;
     cudaError_t e0 = once_status(once, once_st, [&] {
-      return cudaFuncSetAttribute(k1d_sym_kernel<T, TR, SC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      return cudaFuncSetAttribute(k1d_sym_kernel<T, TR, SC, NT, RD, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)K1D_SMEM_MAX);
     });
     if (e0 != cudaSuccess) return e0;
     const long blocks = (n_pts / TR) * ((n_vec + SC - 1) / SC);
-    k1d_sym_kernel<T, TR, SC, NT><<<(unsigned)blocks, NT, smem, st>>>(n_vec, n_occ, n3, a, tau4, L, vloc, vh,
+    k1d_sym_kernel<T, TR, SC, NT, RD, RT><<<(unsigned)blocks, NT, smem, st>>>(n_vec, n_occ, n3, a, tau4, L, vloc, vh,
                                                                       upsi, (T)sf, out);
     note_launch();
     return cudaGetLastError();
@@ -365,7 +463,7 @@ int k1d_sym_num_variants() { return kNumVariants; }
 template <typename T>
 bool k1d_sym_fits(int n_occ, int v) {
   if (v < 1 || v > kNumVariants) return false;
-  if (sizeof(T) == 8 && kVariants[v].sc >= 8) return false;
+  if (sizeof(T) == 8 && (kVariants[v].sc >= 8 || kVariants[v].rd > 0 || kVariants[v].rt > 0)) return false;
   return variant_smem<T>(n_occ, v) <= K1D_SMEM_MAX;
 }
 
@@ -419,6 +517,16 @@ cudaError_t k1d_sym_tiled(int n_vec, int n_occ, long n3, const T* a, const T* ta
     BSE_K1D_CASE(10, 16, 1, 256)
     BSE_K1D_CASE(11, 32, 4, 512)
     BSE_K1D_CASE(12, 32, 2, 256)
+#define BSE_K1D_RING(V, TR, SC, NT, RD, RT) \
+  case V: return launch_k1d<T, TR, SC, NT, RD, RT>(n_vec, n_occ, n3, a, tau4, L, vloc, vh, upsi, sf, out, n_pts, st);
+    BSE_K1D_RING(13, 8, 4, 256, 12, 3)
+    BSE_K1D_RING(14, 8, 4, 256, 8, 4)
+    BSE_K1D_RING(15, 8, 2, 256, 8, 1)
+    BSE_K1D_RING(16, 8, 8, 256, 8, 2)
+    BSE_K1D_RING(17, 8, 4, 256, 16, 2)
+    BSE_K1D_RING(18, 8, 2, 256, 4, 2)
+    BSE_K1D_RING(19, 16, 2, 256, 8, 1)
+#undef BSE_K1D_RING
     default: return cudaErrorInvalidValue;
   }
 #undef BSE_K1D_CASE

@@ -178,6 +178,26 @@ def test_once_per_pair_tau_vs_matrix_free(ragged_case, prec, tol, monkeypatch):
         assert rel(o.double().cpu().numpy(), ref[:n]) <= tol
 
 
+# every kernel variant for tau stored once per pair (register rings, then shared-memory
+# rings), fixed through BSE_K1D_SYM_VARIANT; a variant that does not fit the precision is
+# ignored by the library and the test then checks the tuned choice
+@pytest.mark.parametrize("variant", range(1, 20))
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
+def test_once_per_pair_variants_vs_matrix_free(ragged_case, variant, prec, tol, monkeypatch):
+    inst, A, ref = ragged_case
+    monkeypatch.setenv("BSE_TAU_LAYOUT", "upper")
+    monkeypatch.setenv("BSE_K1D_SYM_VARIANT", str(variant))
+    c = ctx_for(inst, prec)
+    a = dev(A, prec)
+    out = torch.empty_like(a)
+    c.apply(a, out)
+    got = out.double().cpu().numpy()
+    assert rel(got, ref) <= tol, (variant, rel(got, ref))
+    o = torch.empty_like(a[:2])                 # a narrow block: one partial vector chunk
+    c.apply(a[:2].contiguous(), o)
+    assert rel(o.double().cpu().numpy(), ref[:2]) <= tol, variant
+
+
 @pytest.mark.parametrize("variant", range(1, 21))
 @pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
 def test_k1d_tile_variants_vs_matrix_free(ragged_case, variant, prec, tol, monkeypatch):
