@@ -466,8 +466,12 @@ __device__ __forceinline__ void cp_async_wait_all_groups() { asm volatile("cp.as
 // (g, z) planes. Twiddles and x slots are set up once per CTA; in the inverse the next
 // plane's columns are copied (cp.async, 16 bytes per copy where aligned) into a prefetch
 // buffer while the current plane is transformed.
+// threads of a plane CTA: 512 where one CTA fills an SM's shared memory (the 96^3 grid), so
+// that SM still runs 16 warps; 256 elsewhere
+template <int N> constexpr int plane_threads() { return N >= 96 ? 512 : 256; }
+
 template <typename T, int N, bool INV>
-__global__ void __launch_bounds__(256) sph_plane_kernel(cplx<T>* __restrict__ I1, cplx<T>* __restrict__ grid,
+__global__ void __launch_bounds__(plane_threads<N>()) sph_plane_kernel(cplx<T>* __restrict__ I1, cplx<T>* __restrict__ grid,
                                                        SphereMap m, int sign, const cplx<T>* __restrict__ table,
                                                        long n_planes) {
   using C = cplx<T>;
@@ -588,8 +592,8 @@ static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>*
       auto it = occ_of.find(std::make_pair(inverse, psmem));
       if (it == occ_of.end()) {
         cudaError_t e = inverse
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sph_plane_kernel<T, N, true>, 256, psmem)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sph_plane_kernel<T, N, false>, 256, psmem);
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sph_plane_kernel<T, N, true>, plane_threads<N>(), psmem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sph_plane_kernel<T, N, false>, plane_threads<N>(), psmem);
         if (e != cudaSuccess) return e;
         occ_of[std::make_pair(inverse, psmem)] = occ;
       } else {
@@ -607,7 +611,7 @@ static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>*
   if (inverse) {
     sph_z_kernel<T, N, true><<<(unsigned)bz, 256, smem, st>>>(S, I1, m, +1, table); note_launch();
     if constexpr (use_plane) {
-      sph_plane_kernel<T, N, true><<<(unsigned)plane_grid, 256, psmem, st>>>(I1, grid, m, +1, table, bp);
+      sph_plane_kernel<T, N, true><<<(unsigned)plane_grid, plane_threads<N>(), psmem, st>>>(I1, grid, m, +1, table, bp);
       note_launch();
     } else {
       sph_y_kernel<T, N, true><<<(unsigned)by, 256, smem, st>>>(I1, I2, m, +1, table); note_launch();
@@ -615,7 +619,7 @@ static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>*
     }
   } else {
     if constexpr (use_plane) {
-      sph_plane_kernel<T, N, false><<<(unsigned)plane_grid, 256, psmem, st>>>(I1, grid, m, -1, table, bp);
+      sph_plane_kernel<T, N, false><<<(unsigned)plane_grid, plane_threads<N>(), psmem, st>>>(I1, grid, m, -1, table, bp);
       note_launch();
     } else {
       sph_x_kernel<T, N, false><<<(unsigned)bx, 256, smem, st>>>(I2, grid, m, -1, table); note_launch();
