@@ -602,8 +602,9 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
     // a_sv(G) -> a_sv(r)
     // a_sv(G) -> a_sv(r): pruned transform, compact stages in the (not yet used) R(r) grids
     {
-      const double gsc = gb * (double)sphere_scratch_per_grid(N, c->sph) / (double)n3;
-      Scope sc(c, "fft_inverse_a", (double)nf * c->n_pw * sz + gb + 2.0 * gsc, fft_flops(n3, ngr));
+      // algorithmic bytes: the sphere read and the grid written once (the compact column stage
+      // in between is the transform's own traffic, not counted)
+      Scope sc(c, "fft_inverse_a", (double)nf * c->n_pw * sz + gb, fft_flops(n3, ngr));
       CK(sphere_to_grid<T>(ain, nf, c->n_pw, c->n_half, N, c->sph, tw_of<T>(c), gr, ga, c->st));
     }
     // Hartree potential of the pair density sum_w psi_w a_sw (Eq. k1e)
@@ -646,8 +647,9 @@ int apply_impl(bse_ctx* c, long n_vec, const T* a_in, T* a_out) {
     // back to the sphere, plus (1/2|G|^2 + Delta - eps_v) a (Eq. d); compact stages in
     // the a(r) grids, which K1d no longer needs
     {
-      const double gsc = gb * (double)sphere_scratch_per_grid(N, c->sph) / (double)n3;
-      Scope sc(c, "fft_forward_r", gb + 2.0 * gsc + 3.0 * nf * c->n_pw * sz, fft_flops(n3, ngr));
+      // algorithmic bytes: the grid read once, the sphere written once and a(G) read once for the
+      // fused diagonal term
+      Scope sc(c, "fft_forward_r", gb + 2.0 * nf * c->n_pw * sz, fft_flops(n3, ngr));
       CK(grid_to_sphere<T>(gr, nf, c->n_pw, c->n_half, N, c->sph, tw_of<T>(c), ga, 1.0 / (double)n3, aout,
                            ain, g2h_of<T>(c), esh_of<T>(c), c->n_occ, c->st));
     }
