@@ -1020,15 +1020,32 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
   CA(al(&pcbuf, (size_t)b * c->n_occ * c->n_occ + 16));
   double ms_apply = 0;
   int n_apply = 0;
+  // operator applications are timed by CUDA events on the context stream (read once the solve
+  // has finished), so timing them does not stall the stream
+  struct ApplyEvents {
+    std::vector<cudaEvent_t> ev;
+    ~ApplyEvents() { for (cudaEvent_t e : ev) cudaEventDestroy(e); }
+  } apply_ev;
   auto timed_apply = [&](long nv, const T* in, T* out) -> int {
-    CK(cudaStreamSynchronize(c->st));
-    const auto t0 = clk::now();
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    apply_ev.ev.push_back(e0);
+    CK(cudaEventCreate(&e1));
+    apply_ev.ev.push_back(e1);
+    CK(cudaEventRecord(e0, c->st));
     int r = apply_impl<T>(c, nv, in, out);
     if (r != BSE_OK) return r;
-    CK(cudaStreamSynchronize(c->st));
-    ms_apply += std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    CK(cudaEventRecord(e1, c->st));
     n_apply += (int)nv;
     return BSE_OK;
+  };
+  auto apply_ms = [&]() {
+    double t = 0;
+    for (size_t i = 0; i + 1 < apply_ev.ev.size(); i += 2) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, apply_ev.ev[i], apply_ev.ev[i + 1]) == cudaSuccess) t += ms;
+    }
+    return t;
   };
   auto proj = [&](long nvec, T* Xp) -> int {
     // P_c row by row in chunks of `b` vectors (cbuf holds b * n_occ x n_occ)
@@ -1282,6 +1299,7 @@ int davidson_impl(bse_ctx* c, const bse_davidson_opts* o, double* omega_out, T* 
   if (stats) {
     stats->iterations = it;
     stats->n_apply = n_apply;
+    ms_apply = apply_ms();
     stats->ms_apply = ms_apply;
     stats->ms_total = std::chrono::duration<double, std::milli>(clk::now() - t_start).count();
     double mx = 0;
