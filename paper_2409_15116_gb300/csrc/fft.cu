@@ -471,9 +471,9 @@ __device__ __forceinline__ void cp_async_wait_all_groups() { asm volatile("cp.as
 template <int N> constexpr int plane_threads() { return N >= 96 ? 512 : 256; }
 
 template <typename T, int N, bool INV>
-__global__ void __launch_bounds__(plane_threads<N>()) sph_plane_kernel(cplx<T>* __restrict__ I1, cplx<T>* __restrict__ grid,
-                                                       SphereMap m, int sign, const cplx<T>* __restrict__ table,
-                                                       long n_planes) {
+__global__ void __launch_bounds__(plane_threads<N>())
+    sph_plane_kernel(cplx<T>* __restrict__ I1, cplx<T>* __restrict__ grid, SphereMap m, int sign,
+                     const cplx<T>* __restrict__ table, long n_planes) {
   using C = cplx<T>;
   constexpr int R0 = Plan2<N>::r0, R1 = Plan2<N>::r1;
   constexpr int NXM = N / 2 + 1;
@@ -591,9 +591,9 @@ static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>*
       std::lock_guard<std::mutex> lk(mu);
       auto it = occ_of.find(std::make_pair(inverse, psmem));
       if (it == occ_of.end()) {
-        cudaError_t e = inverse
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sph_plane_kernel<T, N, true>, plane_threads<N>(), psmem)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sph_plane_kernel<T, N, false>, plane_threads<N>(), psmem);
+        constexpr int NT = plane_threads<N>();
+        cudaError_t e = inverse ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sph_plane_kernel<T, N, true>, NT, psmem)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sph_plane_kernel<T, N, false>, NT, psmem);
         if (e != cudaSuccess) return e;
         occ_of[std::make_pair(inverse, psmem)] = occ;
       } else {

@@ -274,7 +274,9 @@ __global__ void __launch_bounds__(NT, MINB) k1d_tile_kernel(
 // commit group per entry keeps the per-thread wait (cp.async.wait_group D-1) exact. The
 // neighbour index of an entry is broadcast in the group when the entry is consumed.
 template <int D>
-__device__ __forceinline__ void cp_async_wait_ring() { asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 1) : "memory"); }
+__device__ __forceinline__ void cp_async_wait_ring() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 1) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit_one() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async16_cg(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -518,9 +520,14 @@ cudaError_t k1d_tiled(int n_vec, int n_occ, long n3, const T* a, const T* tau4, 
     case 17:
       return launch_k1d<T, 8, 4, 256, 2, true>(n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi,
                                                sf, out, n_pts, st);
-    case 18: return launch_ring<T, 8, 8, 256, 8>(n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi, sf, out, n_pts, st);
-    case 19: return launch_ring<T, 8, 4, 256, 16>(n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi, sf, out, n_pts, st);
-    case 20: return launch_ring<T, 8, 12, 256, 4>(n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi, sf, out, n_pts, st);
+#define BSE_K1D_RING(V, TR, SC, NT, D)                                                                 \
+  case V:                                                                                              \
+    return launch_ring<T, TR, SC, NT, D>(n_vec, n_occ, n3, a, tau4, n_ent, bptr, bw, n_blocks, vloc, vh, upsi, sf, \
+                                         out, n_pts, st);
+    BSE_K1D_RING(18, 8, 8, 256, 8)
+    BSE_K1D_RING(19, 8, 4, 256, 16)
+    BSE_K1D_RING(20, 8, 12, 256, 4)
+#undef BSE_K1D_RING
     default: return cudaErrorInvalidValue;
   }
 #undef BSE_K1D_CASE
