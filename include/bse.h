@@ -152,14 +152,14 @@ int bse_apply_liouville(bse_ctx* ctx, int n_vec, const void* a_in, void* a_out);
  * The r-space workspaces of the call live in one fixed 32 MiB array compiled into the
  * library (every GPU that loads the library holds it until the process exits). No
  * cudaMalloc, cudaFree or allocating library routine is called; the context must
- * still have been created and bse_build_tau run. Limit: 2 * ceil(n_vec*n_occ/2) + 
+ * still have been created and bse_build_tau run. Limit: 2 * ceil(n_vec*n_occ/2) +
  * ceil(n_vec/2) complex grids of N^3 points plus n_vec*n_occ*max(n_occ, n_qp - n_occ)
  * projector coefficients (each part rounded up to 256 bytes) must fit in 32 MiB; larger requests
  * return BSE_ERR_INVALID_ARG with the byte count in bse_last_error(). The projector
  * runs on the SIMT GEMM in both precisions.
  *
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * once for that device; make that first call before any stream capture. All calls share
+ * once for that device. All calls share
  * the one array and it keeps the previous call's contents (the call clears what it
  * reads before writing): calls that overlap on the GPU, on any stream or from any
  * thread, race on it and must be serialised by the caller. Arguments and result as in
