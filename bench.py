@@ -272,6 +272,49 @@ def batch_run(binding, Context, PREC_MIXED, PREC_FP64, n_systems, warmup=1, step
             "status": rc, "status_fp64": rc64, "iterations": [st.iterations for st in stats]}
 
 
+def cufft_comparison(n_grid: int, n_fields: int, ours_inv_us: float, ours_fwd_us: float, reps: int = 10):
+    """cuFFT (through torch.fft) on the unpruned transforms of the same real fields, for comparison.
+
+    Both library forms are timed per real field: r2c/c2r on the half spectrum, and c2c with two real
+    fields packed in one complex transform (the packing the library's own transforms use). cuFFT
+    starts from a full grid of coefficients: it has no sphere scatter or pruning, so it moves more
+    bytes per field than the sphere-to-grid transforms it is compared with."""
+    import torch
+    n = n_grid
+    nb = max(2, min(n_fields, int(1.5e9 // (n ** 3 * 4 * 3))) // 2 * 2)
+    dev = "cuda"
+    g = torch.Generator(device=dev).manual_seed(0)
+    x = torch.randn(nb, n, n, n, device=dev, generator=g)
+    xh = torch.fft.rfftn(x, dim=(1, 2, 3))
+    z = torch.complex(x[0::2], x[1::2])
+    st = torch.cuda.current_stream()
+
+    def timed(f):
+        for _ in range(3):
+            f()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            f()
+            e1.record(st)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sorted(ts)[len(ts) // 2] * 1e3 / nb         # median, us per real field
+
+    r = {"grid": n, "fields_per_launch": nb,
+         "c2r_us_per_field": timed(lambda: torch.fft.irfftn(xh, s=(n, n, n), dim=(1, 2, 3))),
+         "r2c_us_per_field": timed(lambda: torch.fft.rfftn(x, dim=(1, 2, 3))),
+         "c2c_inverse_us_per_field": timed(lambda: torch.fft.ifftn(z, dim=(1, 2, 3))),
+         "c2c_forward_us_per_field": timed(lambda: torch.fft.fftn(z, dim=(1, 2, 3))),
+         "ours_inverse_us_per_field": ours_inv_us, "ours_forward_us_per_field": ours_fwd_us}
+    r["inverse_speedup_vs_c2r"] = r["c2r_us_per_field"] / ours_inv_us if ours_inv_us else None
+    r["forward_speedup_vs_r2c"] = r["r2c_us_per_field"] / ours_fwd_us if ours_fwd_us else None
+    del x, xh, z
+    torch.cuda.empty_cache()
+    return r
+
+
 def batch_mode(args, binding, Context, PREC_MIXED, PREC_FP64):
     r = batch_run(binding, Context, PREC_MIXED, PREC_FP64, args.batch, args.warmup, args.steps)
     print(json.dumps({"mode": "batch", **r}), flush=True)
@@ -465,6 +508,14 @@ def main():
                    "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
 
+    # the sphere<->grid transforms of the timed steps against cuFFT on the same fields
+    fftcmp = None
+    if rank == 0 and "fft_inverse_a" in prof and "fft_forward_r" in prof:
+        n_fields = sum(st_.n_apply for st_ in stats) * inst.n_occ
+        fftcmp = cufft_comparison(inst.n_grid, inst.n_occ,
+                                  prof["fft_inverse_a"]["ms"] * 1e3 / n_fields,
+                                  prof["fft_forward_r"]["ms"] * 1e3 / n_fields)
+
     # end-to-end through the C ABI with host buffers (context creation uploads the inputs)
     e2e = None
     if rank == 0 and not args.no_e2e:
@@ -516,7 +567,8 @@ def main():
                 "max_err_meV_vs_fp64": max_err_mev, "fp64_plain": fp64,
                 "davidson": {"iterations": stats[-1].iterations, "n_apply": stats[-1].n_apply,
                              "ms_apply": stats[-1].ms_apply, "ms_total": stats[-1].ms_total},
-                "omega_ha": [float(x) for x in om_mixed], "regions": regions, "batch": batch}
+                "omega_ha": [float(x) for x in om_mixed], "regions": regions, "batch": batch,
+                "fft_vs_cufft": fftcmp}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
