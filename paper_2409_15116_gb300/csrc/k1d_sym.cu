@@ -421,7 +421,10 @@ constexpr Variant kVariants[] = {{0, 0, 0, 0, 0},    {8, 4, 256, 0, 0},  {8, 8, 
                                  {32, 2, 256, 0, 0},
                                  // shared-memory rings (single precision): upper depth, tiles in flight
                                  {8, 4, 256, 12, 3}, {8, 4, 256, 8, 4},  {8, 2, 256, 8, 1},  {8, 8, 256, 8, 2},
-                                 {8, 4, 256, 16, 2}, {8, 2, 256, 4, 2},  {16, 2, 256, 8, 1}};
+                                 {8, 4, 256, 16, 2}, {8, 2, 256, 4, 2},  {16, 2, 256, 8, 1},
+                                 // 2-vector chunks of 8 points: both in registers, then one of the two
+                                 // streams (upper entries, tiles) in a shared-memory ring
+                                 {8, 2, 256, 0, 0},  {8, 2, 256, 8, 0},  {8, 2, 256, 0, 2}};
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0])) - 1;
 
 template <typename T>
@@ -526,6 +529,12 @@ cudaError_t k1d_sym_tiled(int n_vec, int n_occ, long n3, const T* a, const T* ta
     BSE_K1D_RING(17, 8, 4, 256, 16, 2)
     BSE_K1D_RING(18, 8, 2, 256, 4, 2)
     BSE_K1D_RING(19, 16, 2, 256, 8, 1)
+#undef BSE_K1D_RING
+    BSE_K1D_CASE(20, 8, 2, 256)
+#define BSE_K1D_RING(V, TR, SC, NT, RD, RT) \
+  case V: return launch_k1d<T, TR, SC, NT, RD, RT>(n_vec, n_occ, n3, a, tau4, L, vloc, vh, upsi, sf, out, n_pts, st);
+    BSE_K1D_RING(21, 8, 2, 256, 8, 0)
+    BSE_K1D_RING(22, 8, 2, 256, 0, 2)
 #undef BSE_K1D_RING
     default: return cudaErrorInvalidValue;
   }

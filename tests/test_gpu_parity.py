@@ -181,7 +181,7 @@ def test_once_per_pair_tau_vs_matrix_free(ragged_case, prec, tol, monkeypatch):
 # every kernel variant for tau stored once per pair (register rings, then shared-memory
 # rings), fixed through BSE_K1D_SYM_VARIANT; a variant that does not fit the precision is
 # ignored by the library and the test then checks the tuned choice
-@pytest.mark.parametrize("variant", range(1, 20))
+@pytest.mark.parametrize("variant", range(1, 23))
 @pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
 def test_once_per_pair_variants_vs_matrix_free(ragged_case, variant, prec, tol, monkeypatch):
     inst, A, ref = ragged_case
