@@ -490,7 +490,8 @@ def main():
     # DRAM traffic per launch of the K1d kernel (model): its entry-major tau once (four slots
     # per entry of the row-block neighbour lists), a(r) and the result once, V_loc, V_H and
     # u_psi. The ncu capture of the op256 launch (32 vectors, 32^3 grid) read and wrote 4.311
-    # GB where this model gives 4.331 GB; the algorithmic bytes count tau once per pair.
+    # GB where this model gives 4.331 GB, and of the 8-point, 8-vector tile with L2 prefetch
+    # at 16 vectors 3.379 GB against 3.255 GB; the algorithmic bytes count tau once per pair.
     traffic = None
     if name == "k1d_combine":
         pr = ctx.pairs()
