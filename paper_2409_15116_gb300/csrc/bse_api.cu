@@ -1643,7 +1643,8 @@ int bse_create(const bse_system* s, int precision, bse_alloc_fn alloc_fn, bse_fr
   // workspace budget: BSE_WORKSPACE_GB or 40% of free memory, at most 64 GB
   {
     size_t fr = 0, tot = 0;
-    cudaMemGetInfo(&fr, &tot);
+    const cudaError_t em = cudaMemGetInfo(&fr, &tot);
+    if (em != cudaSuccess) return bail(cuda_fail(c, em, "cudaMemGetInfo"));
     size_t bud = std::min<size_t>((size_t)64 << 30, (size_t)(0.4 * (double)fr));
     if (const char* e = getenv("BSE_WORKSPACE_GB")) bud = (size_t)(atof(e) * (double)(1ull << 30));
     if (const char* e = getenv("BSE_AUTOTUNE")) c->autotune = atoi(e) != 0;
