@@ -7,7 +7,9 @@ row. Cases:
   * the medium workload itself (72^3 grid, 256 orbitals, 512 PDEP vectors, 4,934 pairs),
     with a block width the Davidson solve applies (13 vectors);
   * the op256 family (32^3 grid, 256 orbitals) with 32 vectors (several vector chunks);
-  * a 72^3 grid with 64 orbitals, every row compared.
+  * a 72^3 grid with 64 orbitals, every row compared;
+  * the large workload (96^3 grid, 1,024 orbitals, tau once per pair) in its bench launch
+    configuration, sampled rows of two vectors.
 These reach the 256-orbital a(r) stage, many row blocks, the transposed tau tiles of late
 blocks, the autotuned tile variants and the multi-tile BF16x3 projector.
 Tolerances as in the other parity tests: FP64 1e-11, mixed 2e-5 relative.
@@ -78,3 +80,36 @@ def test_grid72_64_orbitals_every_row(prec, tol, layout, monkeypatch):
     inst = make_localized(12, 20.0, 72, 64, 2.5, 128, n_eig=4, block=4)
     err = _run(inst, prec, 5, None, 31)
     assert err <= tol, err
+
+
+def test_large_operator_sampled_rows(monkeypatch):
+    """The large workload (96^3 grid, 1,024 orbitals, ~20k pairs, tau once per pair) in the
+    launch configuration of its bench line: a 48 GB r-space workspace, so 7 vectors run as a
+    6-vector chunk and a 1-vector chunk. Rows of the first row block, a middle one and the last
+    one, for the first vector and the one in the second chunk (the oracle transforms all 1,024
+    orbitals of every vector it checks, about a minute each)."""
+    free, total = torch.cuda.mem_get_info()
+    if total < 200e9:
+        pytest.skip("the large workload needs a device of more than 200 GB")
+    from paper_2409_15116_gb300 import Context
+    monkeypatch.setenv("BSE_WORKSPACE_GB", "48")
+    inst = make_config("large")
+    Lop = liouville.Liouville(inst)
+    c = Context(inst, 1)
+    c.build_tau()
+    assert (c.pairs() == pairs.pair_list(Lop.mask)).all()
+    rng = np.random.default_rng(41)
+    n_vec = 7
+    A = Lop.project(rng.standard_normal((n_vec, inst.n_occ, inst.n_pw)))
+    a = torch.tensor(A, dtype=torch.float32, device="cuda")
+    out = torch.empty_like(a)
+    c.apply(a, out)
+    got = out.double().cpu().numpy()
+    c.close()
+    del a, out
+    torch.cuda.empty_cache()
+    rows = [0, 3, 509, 1022, 1023]
+    for k in (0, n_vec - 1):
+        ref = Lop.apply(A[k:k + 1], rows=rows)[0]
+        err = float(np.abs(got[k, rows] - ref[rows]).max() / np.abs(ref[rows]).max())
+        assert err <= 2e-5, (k, err)
