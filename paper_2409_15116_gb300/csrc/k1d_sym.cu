@@ -16,7 +16,10 @@
 // memory by cp.async, groups of TR lanes walking row blocks with four-row register
 // accumulators, upper entries through a register ring of PD 16-byte loads, transposed tiles
 // through a ring of TD tiles; the first CTA of each 32-point tile asks L2 to prefetch each of
-// its groups' next row block (bulk prefetch, no registers or shared memory held).
+// its groups' next row block (bulk prefetch, no registers or shared memory held). Variants with
+// RD > 0 or RT > 0 keep the upper entries or the tiles in flight in shared-memory rings filled by
+// cp.async instead, which frees registers but passes every tau value through shared memory
+// twice; for 1,024 orbitals (2-vector chunks) the all-register form is the fastest.
 #include "common.cuh"
 #include "kernels.h"
 
