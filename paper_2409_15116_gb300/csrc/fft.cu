@@ -437,16 +437,22 @@ __device__ __forceinline__ void pstage(int Ns, int sign, int n_lines, const C* t
   }
 }
 
-template <typename T, int N>
+// rows of the buffer shared by column buffer B and the row block of the x passes: the x lines of
+// a plane run in XH passes of N / XH rows each
+template <int N, int XH>
+constexpr int plane_rows() { return (N / XH > N / 2 + 1) ? N / XH : N / 2 + 1; }
+
+template <typename T, int N, int XH = 1>
 constexpr size_t plane_smem_base() {
-  // column buffer A [NX <= N/2 + 1 slots] + (column buffer B | row plane P) + twiddles + slots
+  // column buffer A [NX <= N/2 + 1 slots] + (column buffer B | row block P) + twiddles + slots
   constexpr int NXM = N / 2 + 1;
-  return (size_t)(NXM * PPad<N>::LS + N * PPad<N>::LS + N) * sizeof(cplx<T>) + (size_t)N * sizeof(int);
+  return (size_t)(NXM * PPad<N>::LS + plane_rows<N, XH>() * PPad<N>::LS + N) * sizeof(cplx<T>) +
+         (size_t)N * sizeof(int);
 }
 // plus, for the inverse, the prefetched columns of the next plane (NC values)
-template <typename T, int N>
+template <typename T, int N, int XH = 1>
 size_t plane_smem(bool inverse, int NC) {
-  return plane_smem_base<T, N>() + (inverse ? (size_t)NC * sizeof(cplx<T>) + 16 : 0);
+  return plane_smem_base<T, N, XH>() + (inverse ? (size_t)NC * sizeof(cplx<T>) + 16 : 0);
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -466,11 +472,16 @@ __device__ __forceinline__ void cp_async_wait_all_groups() { asm volatile("cp.as
 // (g, z) planes. Twiddles and x slots are set up once per CTA; in the inverse the next
 // plane's columns are copied (cp.async, 16 bytes per copy where aligned) into a prefetch
 // buffer while the current plane is transformed.
-// threads of a plane CTA: 512 where one CTA fills an SM's shared memory (the 96^3 grid), so
-// that SM still runs 16 warps; 256 elsewhere
+// threads of a plane CTA: 512 on the 96^3 grid (a 96-point line stage has 768 to 1,152
+// butterflies; two such CTAs per SM measured fastest), 256 elsewhere
 template <int N> constexpr int plane_threads() { return N >= 96 ? 512 : 256; }
 
-template <typename T, int N, bool INV>
+// x passes per plane: two on the 96^3 grid in single precision, where the half-height row block
+// leaves room for two CTAs per SM (forward 15.6 -> 13.0 ms, inverse 14.4 -> 12.9 ms per 6-vector
+// launch of the large workload); one elsewhere (two measured within 2% on the 72^3 grid)
+template <typename T, int N> constexpr int plane_xh() { return (N >= 96 && sizeof(T) == 4) ? 2 : 1; }
+
+template <typename T, int N, bool INV, int XH = 1>
 __global__ void __launch_bounds__(plane_threads<N>())
     sph_plane_kernel(cplx<T>* __restrict__ I1, cplx<T>* __restrict__ grid, SphereMap m, int sign,
                      const cplx<T>* __restrict__ table, long n_planes) {
@@ -480,10 +491,11 @@ __global__ void __launch_bounds__(plane_threads<N>())
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* colA = reinterpret_cast<C*>(smem_raw);          // [NXM][LS]
   C* colB = colA + NXM * PPad<N>::LS;                // [NXM][LS], shares space with P
-  C* P = colB;                                       // [N][LS]
-  C* tw = P + N * PPad<N>::LS;
+  C* P = colB;                                       // [N / XH][LS]
+  C* tw = P + plane_rows<N, XH>() * PPad<N>::LS;
   int* slot = reinterpret_cast<int*>(tw + N);        // slot of x in the band, -1 outside
-  C* pre = reinterpret_cast<C*>(smem_raw + ((plane_smem_base<T, N>() + 15) & ~(size_t)15));  // [NC], inverse
+  C* pre = reinterpret_cast<C*>(smem_raw + ((plane_smem_base<T, N, XH>() + 15) & ~(size_t)15));  // [NC], inverse
+  constexpr int NY = N / XH;                         // rows of one x pass
   load_twiddles<C, N>(tw, table, sign);
   for (int x = threadIdx.x; x < N; x += blockDim.x) slot[x] = -1;
   __syncthreads();
@@ -520,23 +532,33 @@ __global__ void __launch_bounds__(plane_threads<N>())
       pstage<C, N, R1, true>(R0, sign, nx, tw, [&](int l, int q) { return colB[lidx<N>(l, q)]; },
                              [&](int l, int q, C v) { colA[lidx<N>(l, q)] = v; });
       __syncthreads();
-      // x lines: the first stage reads the band from the column buffer (zero outside it),
-      // the second writes the plane to global memory
-      pstage<C, N, R0, true>(1, sign, N, tw,
-                             [&](int y, int x) { const int s = slot[x]; return s >= 0 ? colA[lidx<N>(s, y)] : cmk<C>(0, 0); },
-                             [&](int y, int x, C v) { P[lidx<N>(y, x)] = v; });
-      __syncthreads();
-      pstage<C, N, R1, false>(R0, sign, N, tw, [&](int y, int x) { return P[lidx<N>(y, x)]; },
-                              [&](int y, int x, C v) { Gp[y * N + x] = v; });
+      // x lines, NY rows per pass: the first stage reads the band from the column buffer (zero
+      // outside it), the second writes the rows to global memory
+#pragma unroll 1
+      for (int h = 0; h < XH; ++h) {
+        const int y0 = h * NY;
+        pstage<C, N, R0, true>(1, sign, NY, tw,
+                               [&](int y, int x) { const int s = slot[x]; return s >= 0 ? colA[lidx<N>(s, y0 + y)] : cmk<C>(0, 0); },
+                               [&](int y, int x, C v) { P[lidx<N>(y, x)] = v; });
+        __syncthreads();
+        pstage<C, N, R1, false>(R0, sign, NY, tw, [&](int y, int x) { return P[lidx<N>(y, x)]; },
+                                [&](int y, int x, C v) { Gp[(y0 + y) * N + x] = v; });
+        if (h + 1 < XH) __syncthreads();             // the next pass overwrites P
+      }
     } else {
       __syncthreads();                                // the previous plane's gather is done with colA
-      // x lines: the first stage reads the plane from global memory, the second keeps the band
-      pstage<C, N, R0, false>(1, sign, N, tw, [&](int y, int x) { return Gp[y * N + x]; },
-                              [&](int y, int x, C v) { P[lidx<N>(y, x)] = v; });
-      __syncthreads();
-      pstage<C, N, R1, true>(R0, sign, N, tw, [&](int y, int x) { return P[lidx<N>(y, x)]; },
-                             [&](int y, int x, C v) { const int s = slot[x]; if (s >= 0) colA[lidx<N>(s, y)] = v; });
-      __syncthreads();
+      // x lines, NY rows per pass: the first stage reads the rows from global memory, the
+      // second keeps the band
+#pragma unroll 1
+      for (int h = 0; h < XH; ++h) {
+        const int y0 = h * NY;
+        pstage<C, N, R0, false>(1, sign, NY, tw, [&](int y, int x) { return Gp[(y0 + y) * N + x]; },
+                                [&](int y, int x, C v) { P[lidx<N>(y, x)] = v; });
+        __syncthreads();
+        pstage<C, N, R1, true>(R0, sign, NY, tw, [&](int y, int x) { return P[lidx<N>(y, x)]; },
+                               [&](int y, int x, C v) { const int s = slot[x]; if (s >= 0) colA[lidx<N>(s, y0 + y)] = v; });
+        __syncthreads();
+      }
       // y lines of the band: A -> B -> A
       pstage<C, N, R0, true>(1, sign, nx, tw, [&](int l, int q) { return colA[lidx<N>(l, q)]; },
                              [&](int l, int q, C v) { colB[lidx<N>(l, q)] = v; });
@@ -554,8 +576,10 @@ static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>*
                                  long n_grids, const SphereMap& m, const cplx<T>* table, cudaStream_t st) {
   constexpr int TL = Plan<N>::TX;
   const size_t smem = (size_t)(2 * TL * Pad<N>::LS + N) * sizeof(cplx<T>);
-  const size_t psmem = plane_smem<T, N>(inverse, m.NC);
-  constexpr bool use_plane = plane_smem_base<T, N>() <= 200 * 1024;
+  constexpr int XH = plane_xh<T, N>();
+  constexpr int PNT = plane_threads<N>();
+  const size_t psmem = plane_smem<T, N, XH>(inverse, m.NC);
+  constexpr bool use_plane = plane_smem_base<T, N, XH>() <= 200 * 1024;
   static std::once_flag once;
   static cudaError_t once_st = cudaSuccess;
   static int n_sm = 0;
@@ -568,9 +592,9 @@ static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>*
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if constexpr (use_plane) {
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sph_plane_kernel<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        e = cudaFuncSetAttribute(sph_plane_kernel<T, N, true, XH>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sph_plane_kernel<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        e = cudaFuncSetAttribute(sph_plane_kernel<T, N, false, XH>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     }
     if (e == cudaSuccess) {
       int dev = 0;
@@ -591,9 +615,8 @@ static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>*
       std::lock_guard<std::mutex> lk(mu);
       auto it = occ_of.find(std::make_pair(inverse, psmem));
       if (it == occ_of.end()) {
-        constexpr int NT = plane_threads<N>();
-        cudaError_t e = inverse ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sph_plane_kernel<T, N, true>, NT, psmem)
-                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sph_plane_kernel<T, N, false>, NT, psmem);
+        cudaError_t e = inverse ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sph_plane_kernel<T, N, true, XH>, PNT, psmem)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sph_plane_kernel<T, N, false, XH>, PNT, psmem);
         if (e != cudaSuccess) return e;
         occ_of[std::make_pair(inverse, psmem)] = occ;
       } else {
@@ -611,7 +634,7 @@ static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>*
   if (inverse) {
     sph_z_kernel<T, N, true><<<(unsigned)bz, 256, smem, st>>>(S, I1, m, +1, table); note_launch();
     if constexpr (use_plane) {
-      sph_plane_kernel<T, N, true><<<(unsigned)plane_grid, plane_threads<N>(), psmem, st>>>(I1, grid, m, +1, table, bp);
+      sph_plane_kernel<T, N, true, XH><<<(unsigned)plane_grid, PNT, psmem, st>>>(I1, grid, m, +1, table, bp);
       note_launch();
     } else {
       sph_y_kernel<T, N, true><<<(unsigned)by, 256, smem, st>>>(I1, I2, m, +1, table); note_launch();
@@ -619,7 +642,7 @@ static cudaError_t launch_pruned(bool inverse, cplx<T>* S, cplx<T>* I1, cplx<T>*
     }
   } else {
     if constexpr (use_plane) {
-      sph_plane_kernel<T, N, false><<<(unsigned)plane_grid, plane_threads<N>(), psmem, st>>>(I1, grid, m, -1, table, bp);
+      sph_plane_kernel<T, N, false, XH><<<(unsigned)plane_grid, PNT, psmem, st>>>(I1, grid, m, -1, table, bp);
       note_launch();
     } else {
       sph_x_kernel<T, N, false><<<(unsigned)bx, 256, smem, st>>>(I2, grid, m, -1, table); note_launch();
